@@ -1,0 +1,378 @@
+"""Benchmark: map-making hot path on the 256-detector, nside-512 workload (one JSON line).
+
+A step is one complete map-making solve of the workload: the pointing expansion from the
+FP64 quaternions into the FP32 pointing cache, the block-Jacobi preconditioner, the
+right-hand side P^T N^-1 d in FP64, and 50 PCG iterations whose operator is the fused FP32
+P^T N^-1 P apply (FP64 vectors and scalars). `value` counts the samples pushed through the
+P^T N^-1 P operator per second of whole-step time (steps x 50 applies x 268,435,456 samples).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--small]
+Under torchrun (N > 1) each rank solves its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Gsamples/s of P^T N^-1 P apply; CG solve time at residual 1e-8 vs plain FP64 GPU"
+UNIT = "Gsamples/s"
+CG_ITERS = 50
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="reduced workload for quick checks (not a bench line)")
+    ap.add_argument("--no-cg1e8", action="store_true", help="skip the solve-to-1e-8 comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(small: bool):
+    if small:
+        return dict(nside=128, ndet=32, nsamp=1 << 16)
+    return dict(nside=512, ndet=256, nsamp=1 << 20)
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (host-side helper, identity at world size 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_oracle_apply(wl, ndet_sample: int, reps: int = 1):
+    """Time the FP64 oracle's P^T N^-1 P apply on the first ndet_sample detectors (host, 1 thread)."""
+    import oracle as orc
+    ns = wl["nsamp"]
+    qb = synth.satellite_scan(ns)
+    qd = synth.hex_focal_plane(wl["ndet"])[:ndet_sample]
+    pix, c, s, _ = orc.pointing(wl["nside"], qb, qd)
+    taps = np.tile(synth.inverse_noise_taps(), (ndet_sample, 1))
+    x = synth.gaussian_sky(wl["nside"], synth.rng(2, 0))
+    nz = orc.Noise(taps=taps)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        orc.apply_ata(12 * wl["nside"] ** 2, pix, c, s, nz, None, x)
+        times.append(time.perf_counter() - t0)
+    return ndet_sample * ns, times
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: FP64 CPU P^T N^-1 P applies on a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = workload(args.small)
+    ndet_sample = 2 if args.small else 4
+    n, _ = cpu_oracle_apply(wl, ndet_sample, reps=max(1, args.warmup))
+    _, times = cpu_oracle_apply(wl, ndet_sample, reps=args.steps)
+    t = sum(times)
+    value = n * len(times) / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _wl_name(wl), **wl, "cg_iters": CG_ITERS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one FP64 P^T N^-1 P apply per step over {ndet_sample} of {wl['ndet']} detectors "
+                                   f"x {wl['nsamp']} samples (pointing precomputed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _wl_name(wl):
+    return (f"satellite scan, {wl['ndet']} detectors (hex focal plane, radius 5 deg) x {wl['nsamp']} samples, "
+            f"HEALPix nside {wl['nside']}, 1/f + white noise, 64-tap banded N^-1, {CG_ITERS} PCG iterations")
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_19600_gb300 import build as fxbuild
+    fxbuild.build()
+    import paper_2603_19600_gb300 as fx
+    from paper_2603_19600_gb300 import _native as nat
+
+    wl = workload(args.small)
+    nside, ndet, nsamp = wl["nside"], wl["ndet"], wl["nsamp"]
+    S = ndet * nsamp
+    npix = 12 * nside * nside
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---------------- inputs (seeded, synthetic; not timed)
+    q_bore_h = torch.from_numpy(synth.satellite_scan(nsamp)).pin_memory()
+    q_det_h = torch.from_numpy(synth.hex_focal_plane(ndet)).pin_memory()
+    taps = torch.from_numpy(np.tile(synth.inverse_noise_taps(), (ndet, 1)))
+    sky = torch.from_numpy(synth.gaussian_sky(nside, synth.rng(2, 0)))
+    with torch.cuda.stream(stream):
+        q_bore = q_bore_h.to(dev, non_blocking=True)
+        q_det = q_det_h.to(dev, non_blocking=True)
+        P = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_f32", stream=stream)
+        N = fx.Noise.banded(P, taps)
+        d = P.apply(sky.to(dev).float())
+        # 1/f + white noise, FFT-shaped per detector on the device (seeded torch generator)
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 201 + rank)
+        f = torch.fft.rfftfreq(nsamp, d=1.0 / synth.FSAMP_HZ, device=dev, dtype=torch.float64)
+        amp = torch.sqrt(torch.from_numpy(synth.one_over_f_psd(f.cpu().numpy())).to(dev))
+        amp[0] = 0.0
+        for r0 in range(0, ndet, 32):
+            w = torch.randn(min(32, ndet - r0), nsamp, generator=g, device=dev, dtype=torch.float32)
+            nz = torch.fft.irfft(torch.fft.rfft(w, dim=1) * amp.float(), n=nsamp, dim=1)
+            d.view(ndet, nsamp)[r0:r0 + 32] += nz
+        del w, nz
+    stream.synchronize()
+    d_h = d.cpu().pin_memory()
+
+    def step():
+        P.refresh()
+        return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=1e-30,
+                              max_outer=1, true_residual=False, check_every=10)
+
+    # ---------------- warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3) if not args.small else args.warmup):
+            x, valid, info = step()
+    stream.synchronize()
+    assert info.iters == CG_ITERS, info
+
+    # ---------------- timed region: K steps, barrier + sync on both sides, CUDA events on the stream
+    gpu_id = "0"
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    nat.furax_profile_reset()
+    nat.furax_profile_enable(True)
+    launches0 = fx.launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                x, valid, info = step()
+            e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = fx.launch_count() - launches0
+    nat.furax_profile_enable(False)
+    f32_ms, f32_n = nat.furax_profile_read(0)
+    f64_ms, f64_n = nat.furax_profile_read(1)
+    ms_local = e0.elapsed_time(e1)
+    ms_max = reduce_max(ms_local, world, dev)
+    ms_per_step = ms_max / args.steps
+    samples_per_step = S * CG_ITERS
+    value = world * samples_per_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # ---------------- roofline of the dominant kernel (fused FP32 P^T N^-1 P apply)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 12.0 * S + 2.0 * 24.0 * npix
+    apply_ms = f32_ms / max(f32_n, 1)
+    achieved = alg_bytes / (apply_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "fused_f32_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": apply_ms, "timed_launches": f32_n,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded satellite scan, Gaussian sky, FFT-shaped 1/f noise)",
+        "config": {"workload": _wl_name(wl), **wl, "cg_iters": CG_ITERS, "pointing": "expanded each step from FP64 "
+                   "quaternions into an FP32 cache", "l2": "inputs larger than L2 (3.2 GB pointing cache streamed per apply)"},
+        "roofline": roofline,
+        "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
+        "fp64_fused_ms_per_launch": (f64_ms / f64_n) if f64_n else None,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    # ---------------- end to end through the public API: host buffers in, map out
+    if not args.no_e2e:
+        x_h = torch.empty(npix, 3, dtype=torch.float64).pin_memory()
+        h2d = q_bore_h.numel() * 8 + q_det_h.numel() * 8 + d_h.numel() * 4
+        d2h = x_h.numel() * 8
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e2.record(stream)
+            for _ in range(args.steps):
+                q_bore.copy_(q_bore_h, non_blocking=True)
+                q_det.copy_(q_det_h, non_blocking=True)
+                d.copy_(d_h, non_blocking=True)
+                x, valid, info = step()
+                x_h.copy_(x, non_blocking=True)
+            e3.record(stream)
+        stream.synchronize()
+        barrier(world)
+        e2e_ms = reduce_max(e2.elapsed_time(e3), world, dev)
+        out["e2e"] = {"value": world * samples_per_step * args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+
+    # ---------------- solve to a true residual of 1e-8: mixed precision vs plain FP64
+    if rank == 0 and not args.no_cg1e8 and world == 1:
+        res = {}
+        with torch.cuda.stream(stream):
+            P.refresh()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            xm, _, im = fx.mapmaker_cg(P, N, d, maxiter=2000, tol=1e-8, precision="f32", acc="f32", inner_tol=1e-5,
+                                       max_outer=10)
+            stream.synchronize()
+            res["mixed"] = {"seconds": time.perf_counter() - t0, "iters": im.iters, "outer": im.outer,
+                            "true_rel_res": im.true_rel_res, "converged": im.converged}
+            P64 = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_f64", stream=stream)
+            N64 = fx.Noise.banded(P64, taps)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            x64, _, i64 = fx.mapmaker_cg(P64, N64, d, maxiter=400, tol=1e-8, precision="f64")
+            stream.synchronize()
+            res["fp64"] = {"seconds": time.perf_counter() - t0, "iters": i64.iters, "true_rel_res": i64.true_rel_res,
+                           "converged": i64.converged}
+            res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+            v = valid
+            res["map_rel_diff"] = float(torch.linalg.norm(xm[v] - x64[v]) / torch.linalg.norm(x64[v]))
+            P64.close()
+        out["cg_to_1e-8"] = res
+
+    # ---------------- CPU baseline: the FP64 oracle on the host, bounded sample
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        ndet_sample = 2 if args.small else 8
+        n, times = cpu_oracle_apply(wl, ndet_sample, reps=1)
+        out["cpu_baseline"] = {"value": n / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"one FP64 P^T N^-1 P apply over {ndet_sample} of {ndet} detectors x "
+                                         f"{nsamp} samples (pointing precomputed), {times[0]:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

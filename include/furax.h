@@ -1,0 +1,267 @@
+/*
+ * furax.h — C-ABI of the GB300 map-making hot path (libfurax.so).
+ *
+ * The library implements the operators of linear-operator CMB map-making as
+ * stated in the Furax paper (arXiv 2603.19600):
+ *   data model d = P m + n and the estimator m^ = (P^T N^-1 P)^-1 P^T N^-1 d
+ *     (Statement of Need; the Software Design listing "A = (H.T @ N.I @ H).I @ H.T @ N.I"),
+ *   PointingOperator: sky-to-TOD projection with the pointing expanded on the
+ *     fly (Table 3; "Map-making classes"),
+ *   its transpose (Table 1, "A.T"),
+ *   HomothetyOperator / SymmetricBandToeplitzOperator noise weighting (Table 2),
+ *   BJPreconditioner and the solver-backed inverse "A.I(solver=..., preconditioner=...)"
+ *     (Table 1; "Map-making classes"),
+ *   the block decomposition P^T N^-1 P = sum_i P_i^T N_i^-1 P_i over observations
+ *     ("Algebraic reductions"; MultiObservationMapMaker).
+ * Conventions below the operator level (the paper states none) are fixed here:
+ *   quaternions (w, x, y, z), Hamilton product, detector quaternion q_bore (x) q_det;
+ *   line of sight = R(q) z^, orientation = R(q) x^; HEALPix RING pixels;
+ *   weights (1, cos 2psi, sin 2psi) with psi measured from north through east;
+ *   banded N^-1: y_t = sum_{|k|<K} c_|k| x_{t+k} over 0 <= t+k < nsamp.
+ *
+ * Layouts (all row-major, caller-owned):
+ *   observation i has ndet_i detectors, nsamp_i samples, nside_i; npix_i = 12 nside_i^2.
+ *   TOD: observations concatenated, each [ndet_i][nsamp_i]   (sum_i ndet_i*nsamp_i elements)
+ *   map: observations concatenated, each [npix_i][3] = (I,Q,U) (sum_i npix_i pixels)
+ *   q_bore: [sum_i nsamp_i][4] FP64; q_det: [sum_i ndet_i][4] FP64.
+ * Pointers named "device" must be CUDA device pointers (or managed memory) on the
+ * current device; "host" pointers are ordinary host memory. Every call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream) unless
+ * it says it synchronises. Handles are not thread-safe: one stream at a time.
+ *
+ * Errors: every function returns a furax_status. Negative values are errors and
+ * leave outputs unspecified; furax_last_error() returns a thread-local message.
+ * No function aborts, traps or exits on bad input.
+ */
+#ifndef FURAX_H
+#define FURAX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t furax_status;
+#define FURAX_OK 0
+#define FURAX_ENOTCONVERGED 1 /* solver stopped at maxiter above tolerance (not an error) */
+#define FURAX_EINVAL (-1)      /* bad argument: null pointer, size, enum, mismatch */
+#define FURAX_ENOMEM (-2)      /* device allocation failed */
+#define FURAX_ECUDA (-3)       /* a CUDA call failed; message has the CUDA error string */
+#define FURAX_EBADINPUT (-4)   /* data unusable (e.g. no valid pixel to solve for) */
+#define FURAX_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+
+typedef enum { FURAX_F32 = 0, FURAX_F64 = 1 } furax_dtype;
+
+/* Accumulation of P^T into pixels. */
+typedef enum {
+    FURAX_ACC_F64 = 0,       /* FP64 atomic sums per pixel component */
+    FURAX_ACC_F32_KAHAN = 1, /* FP32 sums with every rounding error captured exactly
+                                (atomic two-sum) and summed in a second FP32 word */
+    FURAX_ACC_F32 = 2        /* plain FP32 atomic sums (fastest, least accurate) */
+} furax_acc;
+
+/* How the pointing is held between operator applications. */
+typedef enum {
+    FURAX_POINTING_ON_THE_FLY = 0, /* recompute pixel and weights from quaternions each call */
+    FURAX_POINTING_CACHE_F32 = 1,  /* cache int32 pixel + FP32 (cos 2psi, sin 2psi): 12 B/sample */
+    FURAX_POINTING_CACHE_F64 = 2   /* cache int32 pixel + FP64 weights: 20 B/sample */
+} furax_pointing_mode;
+
+typedef enum { FURAX_NOISE_WHITE = 0, FURAX_NOISE_BANDED = 1 } furax_noise_kind;
+
+typedef struct furax_pointing furax_pointing_t;
+typedef struct furax_noise furax_noise_t;
+
+/* A batch of independent observations (one map each). */
+typedef struct {
+    int32_t n_obs;            /* >= 1 */
+    const int32_t *ndet;      /* host [n_obs], each >= 1 */
+    const int64_t *nsamp;     /* host [n_obs], each >= 1 */
+    const int32_t *nside;     /* host [n_obs], each in [1, 8192] */
+    const double *q_bore;     /* device [sum nsamp][4], unit quaternions (not renormalised) */
+    const double *q_det;      /* device [sum ndet][4], unit quaternions */
+    const double *psi_offset; /* device [sum ndet] polarisation-angle offsets (rad), or NULL */
+} furax_obs_desc;
+
+/* ---------------------------------------------------------------------------------------
+ * Pointing operator P (PointingOperator, Table 3; IndexOperator "projecting skies onto
+ * time-ordered series", Table 2; QU rotation + ideal polariser folded into the weights).
+ * ------------------------------------------------------------------------------------- */
+
+/* Create a pointing operator over `desc`. The quaternion arrays are referenced, not copied:
+ * they must stay valid and unchanged while the handle lives. psi_offset is copied.
+ * Cache modes run the pointing expansion once here. Samples whose quaternion product is
+ * not finite get pixel -1 and are skipped by every operator; their count is available
+ * from furax_pointing_info. Synchronises `stream` once (to read that count).
+ * Errors: EINVAL (bad sizes/pointers/mode), ENOMEM, ECUDA. *out is NULL on error. */
+furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, void *stream,
+                                   furax_pointing_t **out);
+furax_status furax_pointing_destroy(furax_pointing_t *p);
+
+/* Host query: total samples, total pixels, total detectors, number of invalid samples. */
+furax_status furax_pointing_info(const furax_pointing_t *p, int64_t *nsamp_total, int64_t *npix_total,
+                                 int64_t *ndet_total, int64_t *n_invalid);
+
+/* Recompute the cached pixels and weights from the quaternion arrays given at creation (their
+ * contents may have changed, their shapes may not). No-op for FURAX_POINTING_ON_THE_FLY. */
+furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream);
+
+/* Replace the per-detector polarisation-angle offsets (device [sum ndet] rad, or NULL for none).
+ * Weights become (cos 2(psi+delta), sin 2(psi+delta)); pixels do not change. */
+furax_status furax_pointing_set_psi_offset(furax_pointing_t *p, const double *psi_offset, void *stream);
+
+/* Expand the pointing: per sample its pixel within its observation's map (int32, -1 if
+ * invalid) and weights (cos 2psi, sin 2psi) including offsets, in the TOD layout.
+ * pix: device int32 [nsamp_total]; c, s: device [nsamp_total] of dtype w_t. */
+furax_status furax_pointing_expand(const furax_pointing_t *p, int32_t *pix, void *c, void *s,
+                                   int32_t w_t, void *stream);
+
+/* tod = P map: tod[i] = I_p + Q_p cos 2psi_i + U_p sin 2psi_i (0 for invalid samples).
+ * map: device [npix_total][3] of map_t; tod: device [nsamp_total] of tod_t (overwritten).
+ * Arithmetic is FP64 if either dtype is FP64, else FP32. */
+furax_status furax_pointing_apply(const furax_pointing_t *p, const void *map, int32_t map_t,
+                                  void *tod, int32_t tod_t, void *stream);
+
+/* map (+)= P^T tod: map[p] += sum_{i: pix_i = p} tod[i] (1, cos 2psi_i, sin 2psi_i).
+ * accumulate = 0 overwrites map (and hits), 1 adds to it. hits (device int32 [npix_total])
+ * may be NULL; when given it counts samples per pixel. acc selects the accumulation. */
+furax_status furax_pointing_transpose(const furax_pointing_t *p, const void *tod, int32_t tod_t,
+                                      void *map, int32_t map_t, int32_t acc, int32_t *hits,
+                                      int32_t accumulate, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Noise weighting N^-1 (HomothetyOperator sigma^2, Software Design listing; DiagonalOperator;
+ * SymmetricBandToeplitzOperator with direct convolution, Table 2).
+ * ------------------------------------------------------------------------------------- */
+
+/* kind WHITE: params = device FP64 [sum ndet] variances sigma^2 (N^-1 = 1/sigma^2 per detector).
+ * kind BANDED: params = device FP64 [sum ndet][ntaps] taps c_0..c_{K-1} of the symmetric band
+ * (1 <= ntaps <= 64); the band must be positive definite for the solver to converge.
+ * The taps are copied (an FP32 copy is kept for the FP32 path). */
+furax_status furax_noise_create(int32_t kind, const double *params, int32_t ntaps,
+                                const furax_obs_desc *desc, void *stream, furax_noise_t **out);
+furax_status furax_noise_destroy(furax_noise_t *n);
+
+/* out = N^-1 in, per detector, finite section at the ends of each detector stream.
+ * in, out: device [nsamp_total] of dtype; in and out must not overlap. */
+furax_status furax_noise_inv_apply(const furax_noise_t *n, const void *in, void *out, int32_t dtype,
+                                   void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Block-Jacobi preconditioner (BJPreconditioner, "Map-making classes").
+ * ------------------------------------------------------------------------------------- */
+
+/* M_p = sum_{i: pix_i = p} ninv_det(i) w_i w_i^T with w = (1, cos 2psi, sin 2psi) and ninv the
+ * diagonal of N^-1 (1/sigma^2, or tap c_0). Inverted in FP64 per pixel (adjugate); pixel p is
+ * valid iff hits >= 3, det > 0 and rcond = 1/(|M|_1 |M^-1|_1) >= rcond_min.
+ * blocks_inv: device FP64 [npix_total][6] = (00,01,02,11,12,22) of M^-1, 0 where invalid;
+ * valid: device uint8 [npix_total]; hits: device int32 [npix_total] (may be NULL);
+ * rcond: device FP64 [npix_total] (may be NULL). */
+furax_status furax_blockdiag_precond(const furax_pointing_t *p, const furax_noise_t *n, double rcond_min,
+                                     double *blocks_inv, uint8_t *valid, int32_t *hits, double *rcond,
+                                     void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Normal-equations operator and right-hand side ("A = (H.T @ N.I @ H).I @ H.T @ N.I",
+ * Software Design listing; block decomposition P^T N^-1 P = sum_i P_i^T N_i^-1 P_i).
+ * ------------------------------------------------------------------------------------- */
+
+/* out = S P^T N^-1 P S^T x with S the valid-pixel selector (valid may be NULL: all pixels).
+ * x, out: device FP64 [npix_total][3], must not overlap. precision FURAX_F32 runs the
+ * projection, the noise stencil and the weights in FP32 (x rounded to FP32 once) with
+ * accumulation `acc`; FURAX_F64 runs everything in FP64 (acc ignored). One fused pass:
+ * the time-ordered data never reaches device memory. */
+furax_status furax_ptnp_apply(const furax_pointing_t *p, const furax_noise_t *n, const double *x,
+                              double *out, const uint8_t *valid, int32_t precision, int32_t acc,
+                              void *stream);
+
+/* b = S P^T N^-1 d in FP64 (d of dtype d_t, device [nsamp_total]; b device FP64 [npix_total][3]). */
+furax_status furax_rhs(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
+                       const uint8_t *valid, double *b, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Map-maker: preconditioned conjugate gradient ("A.I(solver=..., preconditioner=...)",
+ * Table 1; maximum-likelihood and binned estimators, "Map-making classes").
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t maxiter;       /* cap on PCG iterations per observation (all outer steps together) */
+    double tol;            /* stop when ||b - A x||/||b|| <= tol */
+    int32_t precision;     /* FURAX_F64: plain FP64 PCG. FURAX_F32: mixed precision — inner PCG
+                              with the FP32 operator, outer defect correction with the FP64 operator */
+    int32_t acc;           /* accumulation of the inner operator (FURAX_F32 only) */
+    double inner_tol;      /* FURAX_F32: relative reduction asked of each inner solve (e.g. 1e-5) */
+    int32_t max_outer;     /* FURAX_F32: cap on outer corrections */
+    int32_t use_graph;     /* capture the iteration in a CUDA graph and replay it */
+    int32_t check_every;   /* iterations between host convergence checks (>= 1) */
+    double rcond_min;      /* preconditioner validity threshold (e.g. 1e-3) */
+    int32_t binned_only;   /* 1: return the binned map M^-1 b (no iterations) */
+    int32_t true_residual; /* 1 computes ||b - A64 x||/||b|| at exit (one more application of the
+                              FP64 operator); 0 skips it where it is not needed to continue
+                              (true_rel_res = -1; FURAX_F32 then stops after its last inner solve) */
+} furax_cg_opts;
+
+typedef struct {
+    int32_t iters;          /* PCG iterations performed (max over observations) */
+    int32_t outer;          /* outer corrections performed (FURAX_F32) */
+    double rel_res;         /* final recursive ||r||/||b|| (max over observations) */
+    double true_rel_res;    /* final ||b - A64 x||/||b|| with the FP64 operator (max over observations) */
+    int64_t n_valid;        /* number of solved pixels */
+    double *hist;           /* host, caller-owned, [hist_len] recursive residual of observation 0
+                               per iteration (entry 0 = 1), or NULL */
+    int32_t hist_len;
+    int32_t hist_written;   /* entries written to hist */
+} furax_cg_result;
+
+/* Fill `opts` with defaults: maxiter 50, tol 1e-8, FP64, ACC_F32, inner_tol 1e-5, max_outer 8,
+ * graph on, check_every 10, rcond_min 1e-3, true_residual 1. */
+void furax_cg_default_opts(furax_cg_opts *opts);
+
+/* Solve (S P^T N^-1 P S^T) x = S P^T N^-1 d for every observation independently (per-observation
+ * PCG scalars), x0 = 0, block-Jacobi preconditioner. x: device FP64 [npix_total][3], overwritten,
+ * zero on unsolved pixels. valid (device uint8 [npix_total], may be NULL) receives the mask.
+ * Allocates its workspace, synchronises `stream`, fills `res` (host). Returns FURAX_OK when every
+ * observation reached tol, FURAX_ENOTCONVERGED when the iteration cap was hit first. */
+furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
+                               double *x, uint8_t *valid, const furax_cg_opts *opts, furax_cg_result *res,
+                               void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * chi^2 and its gradients (differentiability, "Summary"; "Research Impact Statement").
+ * ------------------------------------------------------------------------------------- */
+
+/* r = d - P(delta) m; chi2 = r^T N^-1 r; grad_map = -2 P^T N^-1 r;
+ * grad_psi[j] = -2 sum_t (N^-1 r)_{j,t} * 2 (U_p cos 2psi - Q_p sin 2psi) (offsets included).
+ * d device [nsamp_total] of d_t; m device FP64 [npix_total][3]; chi2 device FP64 [n_obs]
+ * (per observation); grad_map device FP64 [npix_total][3] or NULL; grad_psi device FP64
+ * [sum ndet] or NULL. precision FURAX_F32: residual and N^-1 in FP32, sums in FP64. */
+furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
+                             const double *m, double *chi2, double *grad_map, double *grad_psi,
+                             int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics.
+ * ------------------------------------------------------------------------------------- */
+
+/* Thread-local message describing the last error ("" if none). Never NULL. */
+const char *furax_last_error(void);
+/* Number of kernels this library has launched in this process (graph replays count their
+ * kernel nodes). */
+int64_t furax_launch_count(void);
+/* Library version string. */
+const char *furax_version(void);
+
+/* Kernel timing: when enabled, the library brackets every launch of the fused P^T N^-1 P
+ * kernels (FP32 and FP64) with CUDA events on the launching stream (also inside captured
+ * graphs) and accumulates their durations, read at the solver's synchronisation points and
+ * at furax_profile_read. kernel: 0 = FP32 fused apply, 1 = FP64 fused apply (incl. right-hand
+ * side). Writes the total milliseconds and the number of timed launches. */
+void furax_profile_enable(int32_t on);
+furax_status furax_profile_read(int32_t kernel, double *total_ms, int64_t *count);
+void furax_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FURAX_H */

@@ -278,7 +278,10 @@ int64_t orc_pointing(int64_t nside, int64_t nsamp, const double *q_bore, int64_t
                 pix[i] = -1; cw[i] = 0.0; sw[i] = 0.0; ++bad; continue;
             }
             orc_quat_axes(q, d, o);
-            pix[i] = (int32_t)orc_vec2pix_ring(nside, d);
+            /* A quaternion far from unit norm can send the ring index past the last ring: no pixel. */
+            int64_t pp = orc_vec2pix_ring(nside, d);
+            if (pp < 0 || pp >= 12 * nside * nside) { pix[i] = -1; cw[i] = 0.0; sw[i] = 0.0; ++bad; continue; }
+            pix[i] = (int32_t)pp;
             double rho2 = d[0] * d[0] + d[1] * d[1];
             double a = -d[2] * (o[0] * d[0] + o[1] * d[1]) + rho2 * o[2];
             double b = -o[0] * d[1] + o[1] * d[0];

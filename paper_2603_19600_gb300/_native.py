@@ -1,0 +1,279 @@
+"""ctypes binding of libfurax.so: one Python function per C entry point, same names.
+
+Arguments are torch tensors on the current CUDA device (or plain Python values); each
+function checks dtype, device, contiguity and size, passes ``tensor.data_ptr()`` and
+``torch.cuda.current_stream().cuda_stream``, and raises FuraxError on a negative status.
+There is no fallback: if the library is not built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+FURAX_OK = 0
+FURAX_ENOTCONVERGED = 1
+FURAX_F32, FURAX_F64 = 0, 1
+FURAX_ACC_F64, FURAX_ACC_F32_KAHAN, FURAX_ACC_F32 = 0, 1, 2
+FURAX_POINTING_ON_THE_FLY, FURAX_POINTING_CACHE_F32, FURAX_POINTING_CACHE_F64 = 0, 1, 2
+FURAX_NOISE_WHITE, FURAX_NOISE_BANDED = 0, 1
+
+_DT = {torch.float32: FURAX_F32, torch.float64: FURAX_F64}
+
+
+class FuraxError(RuntimeError):
+    def __init__(self, func: str, code: int, msg: str):
+        super().__init__(f"{func} failed with status {code}: {msg}")
+        self.code = code
+
+
+class ObsDesc(ctypes.Structure):
+    _fields_ = [("n_obs", ctypes.c_int32), ("ndet", ctypes.c_void_p), ("nsamp", ctypes.c_void_p),
+                ("nside", ctypes.c_void_p), ("q_bore", ctypes.c_void_p), ("q_det", ctypes.c_void_p),
+                ("psi_offset", ctypes.c_void_p)]
+
+
+class CgOpts(ctypes.Structure):
+    _fields_ = [("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("acc", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("check_every", ctypes.c_int32), ("rcond_min", ctypes.c_double),
+                ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32)]
+
+
+class CgResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("true_rel_res", ctypes.c_double), ("n_valid", ctypes.c_int64),
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("hist_len", ctypes.c_int32),
+                ("hist_written", ctypes.c_int32)]
+
+
+_V, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "furax_pointing_create": [ctypes.POINTER(ObsDesc), _I32, _V, ctypes.POINTER(_V)],
+    "furax_pointing_destroy": [_V],
+    "furax_pointing_info": [_V, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "furax_pointing_refresh": [_V, _V],
+    "furax_pointing_set_psi_offset": [_V, _V, _V],
+    "furax_profile_read": [_I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)],
+    "furax_pointing_expand": [_V, _V, _V, _V, _I32, _V],
+    "furax_pointing_apply": [_V, _V, _I32, _V, _I32, _V],
+    "furax_pointing_transpose": [_V, _V, _I32, _V, _I32, _I32, _V, _I32, _V],
+    "furax_noise_create": [_I32, _V, _I32, ctypes.POINTER(ObsDesc), _V, ctypes.POINTER(_V)],
+    "furax_noise_destroy": [_V],
+    "furax_noise_inv_apply": [_V, _V, _V, _I32, _V],
+    "furax_blockdiag_precond": [_V, _V, _D, _V, _V, _V, _V, _V],
+    "furax_ptnp_apply": [_V, _V, _V, _V, _V, _I32, _I32, _V],
+    "furax_rhs": [_V, _V, _V, _I32, _V, _V, _V],
+    "furax_mapmaker_cg": [_V, _V, _V, _I32, _V, _V, ctypes.POINTER(CgOpts), ctypes.POINTER(CgResult), _V],
+    "furax_chi2_grad": [_V, _V, _V, _I32, _V, _V, _V, _V, _I32, _V],
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfurax.so. Raises if it has not been built: there is no CPU path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfurax.so not found at {path}: build it with "
+                                   "paper_2603_19600_gb300.build.build() (needs nvcc)")
+            torch.cuda.init()
+            l = ctypes.CDLL(path)
+            for name, args in _SIGS.items():
+                f = getattr(l, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int32
+            l.furax_last_error.restype = ctypes.c_char_p
+            l.furax_launch_count.restype = ctypes.c_int64
+            l.furax_version.restype = ctypes.c_char_p
+            l.furax_cg_default_opts.argtypes = [ctypes.POINTER(CgOpts)]
+            l.furax_cg_default_opts.restype = None
+            l.furax_profile_enable.argtypes = [ctypes.c_int32]
+            l.furax_profile_enable.restype = None
+            l.furax_profile_reset.restype = None
+            _lib = l
+    return _lib
+
+
+def _call(name: str, *args, ok=(FURAX_OK,)) -> int:
+    rc = getattr(lib(), name)(*args)
+    if rc < 0 or (rc not in ok and rc < 0):
+        raise FuraxError(name, rc, lib().furax_last_error().decode())
+    return rc
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, numel=None, name="tensor") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype not in _DT:
+        raise ValueError(f"unsupported dtype {t.dtype}")
+    return _DT[t.dtype]
+
+
+def launch_count() -> int:
+    return int(lib().furax_launch_count())
+
+
+def version() -> str:
+    return lib().furax_version().decode()
+
+
+def default_cg_opts() -> CgOpts:
+    o = CgOpts()
+    lib().furax_cg_default_opts(ctypes.byref(o))
+    return o
+
+
+class _Desc:
+    """Keeps the host arrays of an ObsDesc alive."""
+
+    def __init__(self, ndet, nsamp, nside, q_bore=None, q_det=None, psi_offset=None):
+        self.n = len(ndet)
+        self.ndet = (ctypes.c_int32 * self.n)(*[int(v) for v in ndet])
+        self.nsamp = (ctypes.c_int64 * self.n)(*[int(v) for v in nsamp])
+        self.nside = (ctypes.c_int32 * self.n)(*[int(v) for v in nside])
+        self.desc = ObsDesc(self.n, ctypes.cast(self.ndet, _V), ctypes.cast(self.nsamp, _V),
+                            ctypes.cast(self.nside, _V), q_bore, q_det, psi_offset)
+
+
+# ------------------------------------------------------------------ entry points, same names as the C ABI
+def furax_pointing_create(q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode=FURAX_POINTING_CACHE_F32,
+                          stream=None) -> int:
+    nb, nd = sum(int(v) for v in nsamp), sum(int(v) for v in ndet)
+    d = _Desc(ndet, nsamp, nside, _ptr(q_bore, torch.float64, 4 * nb, "q_bore"),
+              _ptr(q_det, torch.float64, 4 * nd, "q_det"), _ptr(psi_offset, torch.float64, nd, "psi_offset"))
+    h = _V()
+    _call("furax_pointing_create", ctypes.byref(d.desc), mode, _stream(stream), ctypes.byref(h))
+    return h.value
+
+
+def furax_pointing_destroy(h) -> None:
+    if h:
+        _call("furax_pointing_destroy", h)
+
+
+def furax_pointing_info(h):
+    a, b, c, d = _I64(), _I64(), _I64(), _I64()
+    _call("furax_pointing_info", h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return dict(nsamp_total=a.value, npix_total=b.value, ndet_total=c.value, n_invalid=d.value)
+
+
+def furax_pointing_refresh(h, stream=None) -> None:
+    _call("furax_pointing_refresh", h, _stream(stream))
+
+
+def furax_profile_enable(on: bool) -> None:
+    lib().furax_profile_enable(int(bool(on)))
+
+
+def furax_profile_reset() -> None:
+    lib().furax_profile_reset()
+
+
+def furax_profile_read(kernel: int):
+    """(total milliseconds, number of timed launches) of kernel 0 (FP32 fused) or 1 (FP64 fused)."""
+    ms, n = _D(), _I64()
+    _call("furax_profile_read", kernel, ctypes.byref(ms), ctypes.byref(n))
+    return ms.value, n.value
+
+
+def furax_pointing_set_psi_offset(h, psi_offset, stream=None) -> None:
+    _call("furax_pointing_set_psi_offset", h, _ptr(psi_offset, torch.float64, None, "psi_offset"), _stream(stream))
+
+
+def furax_pointing_expand(h, pix, c, s, stream=None) -> None:
+    _call("furax_pointing_expand", h, _ptr(pix, torch.int32, None, "pix"), _ptr(c, None, pix.numel(), "c"),
+          _ptr(s, c.dtype, pix.numel(), "s"), _dt(c), _stream(stream))
+
+
+def furax_pointing_apply(h, m, tod, stream=None) -> None:
+    _call("furax_pointing_apply", h, _ptr(m, None, None, "map"), _dt(m), _ptr(tod, None, None, "tod"), _dt(tod),
+          _stream(stream))
+
+
+def furax_pointing_transpose(h, tod, m, acc=FURAX_ACC_F64, hits=None, accumulate=False, stream=None) -> None:
+    _call("furax_pointing_transpose", h, _ptr(tod, None, None, "tod"), _dt(tod), _ptr(m, None, None, "map"), _dt(m),
+          acc, _ptr(hits, torch.int32, None, "hits"), int(bool(accumulate)), _stream(stream))
+
+
+def furax_noise_create(kind, params, ntaps, ndet, nsamp, nside, stream=None) -> int:
+    d = _Desc(ndet, nsamp, nside)
+    h = _V()
+    _call("furax_noise_create", kind, _ptr(params, torch.float64, None, "params"), ntaps, ctypes.byref(d.desc),
+          _stream(stream), ctypes.byref(h))
+    return h.value
+
+
+def furax_noise_destroy(h) -> None:
+    if h:
+        _call("furax_noise_destroy", h)
+
+
+def furax_noise_inv_apply(h, x, out, stream=None) -> None:
+    if x.dtype != out.dtype:
+        raise ValueError("in and out must have the same dtype")
+    _call("furax_noise_inv_apply", h, _ptr(x, None, None, "in"), _ptr(out, None, x.numel(), "out"), _dt(x),
+          _stream(stream))
+
+
+def furax_blockdiag_precond(hp, hn, rcond_min, blocks_inv, valid, hits=None, rcond=None, stream=None) -> None:
+    _call("furax_blockdiag_precond", hp, hn, float(rcond_min), _ptr(blocks_inv, torch.float64, None, "blocks_inv"),
+          _ptr(valid, torch.uint8, None, "valid"), _ptr(hits, torch.int32, None, "hits"),
+          _ptr(rcond, torch.float64, None, "rcond"), _stream(stream))
+
+
+def furax_ptnp_apply(hp, hn, x, out, valid=None, precision=FURAX_F32, acc=FURAX_ACC_F32, stream=None) -> None:
+    _call("furax_ptnp_apply", hp, hn, _ptr(x, torch.float64, None, "x"), _ptr(out, torch.float64, x.numel(), "out"),
+          _ptr(valid, torch.uint8, None, "valid"), precision, acc, _stream(stream))
+
+
+def furax_rhs(hp, hn, d, b, valid=None, stream=None) -> None:
+    _call("furax_rhs", hp, hn, _ptr(d, None, None, "d"), _dt(d), _ptr(valid, torch.uint8, None, "valid"),
+          _ptr(b, torch.float64, None, "b"), _stream(stream))
+
+
+def furax_mapmaker_cg(hp, hn, d, x, valid=None, opts: CgOpts | None = None, hist_len=0, stream=None):
+    o = opts if opts is not None else default_cg_opts()
+    res = CgResult()
+    hist = (ctypes.c_double * max(hist_len, 1))()
+    res.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist_len > 0 else None
+    res.hist_len = hist_len
+    rc = _call("furax_mapmaker_cg", hp, hn, _ptr(d, None, None, "d"), _dt(d), _ptr(x, torch.float64, None, "x"),
+               _ptr(valid, torch.uint8, None, "valid"), ctypes.byref(o), ctypes.byref(res), _stream(stream),
+               ok=(FURAX_OK, FURAX_ENOTCONVERGED))
+    return rc, res, [hist[i] for i in range(res.hist_written)]
+
+
+def furax_chi2_grad(hp, hn, d, m, chi2, grad_map=None, grad_psi=None, precision=FURAX_F64, stream=None) -> None:
+    _call("furax_chi2_grad", hp, hn, _ptr(d, None, None, "d"), _dt(d), _ptr(m, torch.float64, None, "m"),
+          _ptr(chi2, torch.float64, None, "chi2"), _ptr(grad_map, torch.float64, None, "grad_map"),
+          _ptr(grad_psi, torch.float64, None, "grad_psi"), precision, _stream(stream))

@@ -1,0 +1,59 @@
+// Fire-and-forget reductions into global memory (resolved in L2) and the compensated
+// FP32 accumulation used by FURAX_ACC_F32_KAHAN.
+#pragma once
+#include <cstdint>
+
+namespace fx {
+
+__device__ __forceinline__ void red_add_f64(double *a, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(a), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_s32(int32_t *a, int32_t v)
+{
+    asm volatile("red.global.add.s32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// One 16-byte vector reduction: four FP32 adds at the cost of one L2 atomic operation.
+__device__ __forceinline__ void red_add_v4(float4 *a, float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ float4 atom_add_v4(float4 *a, float4 v)
+{
+    float4 r;
+    asm volatile("atom.global.v4.f32.add {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+    return r;
+}
+
+// Rounding error of s = fl(a + b) (Knuth's two-sum): a + b = s + err exactly in
+// round-to-nearest FP32.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// Compensated accumulation: the atomic returns the value it added to, so the exact
+// rounding error of that addition can be recomputed here and accumulated in `lo`.
+// hi + lo then equals the exact sum up to second-order terms, whatever the order in
+// which the atomics were applied.
+__device__ __forceinline__ void kahan_add_v4(float4 *hi, float4 *lo, float4 v)
+{
+    float4 old = atom_add_v4(hi, v);
+    float4 e;
+    e.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
+    e.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
+    e.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
+    e.w = 0.f;
+    red_add_v4(lo, e);
+}
+
+}  // namespace fx

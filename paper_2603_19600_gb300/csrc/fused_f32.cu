@@ -1,0 +1,144 @@
+// Fused tile kernels of the map-making operator (Furax paper: the estimator
+// A = (H.T @ N.I @ H).I @ H.T @ N.I in the Software Design listing, with the block
+// decomposition P^T N^-1 P = sum_i P_i^T N_i^-1 P_i of "Algebraic reductions").
+//
+// One CTA owns one tile: one detector, TILE consecutive samples. It
+//   1. gathers the projected map P x for the tile plus a 63-sample halo on each side into
+//      shared memory (samples outside the detector stream are zeros: finite section),
+//   2. applies N^-1 (white scale, or the 127-term symmetric band, register-blocked),
+//   3. scatters y (1, cos 2psi, sin 2psi) into per-pixel accumulators with L2 reductions.
+// The time-ordered data never leaves the SM. The same skeleton gives the standalone N^-1,
+// the right-hand side P^T N^-1 d and chi^2 with its gradients.
+#include "tile.cuh"
+
+namespace fx {
+
+// ------------------------------------------------------------------------------------
+// FP32 fused apply: acc += P^T N^-1 P x32  (x32: padded FP32 map, zero on masked pixels)
+// ------------------------------------------------------------------------------------
+template <int MODE, int ACC, bool BANDED>
+__global__ void __launch_bounds__(FT) fused_f32_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+                                                       const float4 *__restrict__ x32, float4 *__restrict__ acc_hi,
+                                                       float4 *__restrict__ acc_lo, double *__restrict__ acc64)
+{
+    extern __shared__ float fsm[];
+    float *xs = fsm;                           // [XS]
+    float *taps = xs + XS;                     // [MAXTAPS]
+    float *sc = taps + MAXTAPS;                // [CS]
+    float *ss = sc + CS;                       // [CS]
+    int32_t *spix = reinterpret_cast<int32_t *>(ss + CS);   // [CS]
+
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if constexpr (BANDED) load_taps<float>(nv, gdet, taps);
+
+    const int nload = tl.len + 2 * halo;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tl.t0 - halo + u;
+        float v = 0.f, c = 0.f, s = 0.f;
+        int32_t pix = -1;
+        if (t >= 0 && t < ob.nsamp) {
+            pix = get_sample<MODE, float>(pv, ob, tl.det, t, c, s);
+            if (pix >= 0) {
+                const float4 m = __ldg(x32 + ob.map_off + pix);
+                v = fmaf(m.z, s, fmaf(m.y, c, m.x));
+            }
+        }
+        xs[spos(u)] = v;
+        const int core = u - halo;
+        if (core >= 0 && core < tl.len) { spix[spos(core)] = pix; sc[spos(core)] = c; ss[spos(core)] = s; }
+    }
+    __syncthreads();
+
+    const int base = threadIdx.x * FR;
+    if (base >= tl.len) return;
+    float y[FR];
+    if constexpr (BANDED) {
+        band_product<float, FR>(xs, taps, base, y);
+    } else {
+        const float w = white_scale<float>(nv, gdet);
+#pragma unroll
+        for (int r = 0; r < FR; ++r) y[r] = xs[spos(base + r)] * w;
+    }
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        const int k = base + r;
+        if (k >= tl.len) break;
+        const int32_t pix = spix[spos(k)];
+        if (pix < 0) continue;
+        const float c = sc[spos(k)], s = ss[spos(k)];
+        const int64_t gp = ob.map_off + pix;
+        const float4 v = make_float4(y[r], y[r] * c, y[r] * s, 0.f);
+        if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
+        else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
+        else {
+            red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
+            red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
+            red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
+        }
+    }
+}
+
+template <int MODE, bool BANDED>
+static furax_status dispatch_fused_f32_acc(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
+                                           float4 *hi, float4 *lo, double *a64, cudaStream_t st)
+{
+    const unsigned g = (unsigned)p->n_tiles;
+    const PointingView pv = p->view();
+    const NoiseView nv = n->view();
+    if (acc == FURAX_ACC_F32)
+        return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F32, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv, x32,
+                          hi, lo, a64);
+    if (acc == FURAX_ACC_F32_KAHAN)
+        return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F32_KAHAN, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv,
+                          x32, hi, lo, a64);
+    return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F64, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv, x32, hi,
+                      lo, a64);
+}
+
+template <int MODE>
+static furax_status dispatch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
+                                       float4 *hi, float4 *lo, double *a64, cudaStream_t st)
+{
+    if (n->kind == FURAX_NOISE_BANDED) return dispatch_fused_f32_acc<MODE, true>(p, n, x32, acc, hi, lo, a64, st);
+    return dispatch_fused_f32_acc<MODE, false>(p, n, x32, acc, hi, lo, a64, st);
+}
+
+furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
+                              float4 *lo, double *a64, cudaStream_t st)
+{
+    if (p->n_tiles == 0) return FURAX_OK;
+    furax_status rc;
+    if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
+    else if (p->mode == FURAX_POINTING_CACHE_F32) rc = dispatch_fused_f32<1>(p, n, x32, acc, hi, lo, a64, st);
+    else rc = dispatch_fused_f32<2>(p, n, x32, acc, hi, lo, a64, st);
+    if (rc) return rc;
+    count_launches(1);
+    return check_launch("fused P^T N^-1 P (FP32)");
+}
+
+template <int MODE, bool B>
+static furax_status prep_f32_mode_band()
+{
+    furax_status rc = FURAX_OK;
+    if (!rc) rc = allow_smem((const void *)fused_f32_kernel<MODE, FURAX_ACC_F32, B>, kF32Smem);
+    if (!rc) rc = allow_smem((const void *)fused_f32_kernel<MODE, FURAX_ACC_F32_KAHAN, B>, kF32Smem);
+    if (!rc) rc = allow_smem((const void *)fused_f32_kernel<MODE, FURAX_ACC_F64, B>, kF32Smem);
+    return rc;
+}
+
+furax_status prepare_fused_f32()
+{
+    furax_status rc = FURAX_OK;
+    if (!rc) rc = prep_f32_mode_band<0, true>();
+    if (!rc) rc = prep_f32_mode_band<0, false>();
+    if (!rc) rc = prep_f32_mode_band<1, true>();
+    if (!rc) rc = prep_f32_mode_band<1, false>();
+    if (!rc) rc = prep_f32_mode_band<2, true>();
+    if (!rc) rc = prep_f32_mode_band<2, false>();
+    return rc;
+}
+
+}  // namespace fx

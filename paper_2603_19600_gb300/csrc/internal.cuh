@@ -1,0 +1,198 @@
+// Internal declarations shared by the CUDA translation units of libfurax.
+#pragma once
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "furax.h"
+
+namespace fx {
+
+constexpr int TILE = 4096;      // samples per work tile (one detector, contiguous in time)
+constexpr int PTILE = 4096;     // pixels per pixel tile (vector kernels, per-observation reductions)
+constexpr int MAXTAPS = 64;     // longest supported symmetric band (c_0..c_63)
+
+struct ObsInfo {
+    int64_t nsamp;     // samples per detector
+    int64_t det_off;   // first detector (global index into q_det / noise parameters)
+    int64_t bore_off;  // first boresight sample (global index into q_bore)
+    int64_t tod_off;   // first TOD element
+    int64_t map_off;   // first pixel of this observation's map
+    int64_t npix;      // 12 nside^2
+    int64_t ptile0;    // first pixel tile of this observation
+    int32_t nptile;    // number of pixel tiles
+    int32_t ndet;
+    int32_t nside;
+    int32_t pad;
+};
+
+struct Tile {          // one detector, samples [t0, t0+len)
+    int64_t t0;
+    int32_t obs;
+    int32_t det;       // local detector index within the observation
+    int32_t len;
+    int32_t pad;
+};
+
+struct PTile {         // pixels [p0, p0+len) of one observation (global map indices)
+    int64_t p0;
+    int32_t obs;
+    int32_t len;
+};
+
+// Everything a kernel needs to know about the pointing; passed by value.
+struct PointingView {
+    const ObsInfo *obs;
+    const double *q_bore;
+    const double *q_det;
+    const double2 *psi_cs;  // per global detector (cos 2 delta, sin 2 delta), or nullptr
+    const int32_t *pix;     // cache (modes 1, 2)
+    const float *c32, *s32; // cache mode 1
+    const double *c64, *s64;// cache mode 2
+};
+
+struct NoiseView {
+    int32_t kind;           // FURAX_NOISE_WHITE / BANDED
+    int32_t ntaps;
+    const double *p64;      // white: inverse variance [ndet]; banded: taps [ndet][ntaps]
+    const float *p32;
+    const double *diag;     // diagonal of N^-1 per detector [ndet] (FP64)
+};
+
+// Status helpers (thread-local message).
+furax_status set_error(furax_status code, const char *fmt, ...);
+furax_status check_cuda(cudaError_t e, const char *what);
+furax_status check_launch(const char *what);
+void count_launches(int64_t n);
+
+// Kernel timing (furax_profile_*): kind 0 = FP32 fused apply, 1 = FP64 fused apply.
+bool prof_on();
+void prof_pair(cudaEvent_t *a, cudaEvent_t *b);          // two events from the pool
+void prof_push(int kind, cudaEvent_t a, cudaEvent_t b);  // recorded pair, read later
+void prof_add(int kind, double ms);
+void prof_flush();                                       // wait for pending pairs, accumulate
+
+// Raise a kernel's dynamic shared-memory limit once (per process, per kernel), then launch.
+furax_status allow_smem(const void *kern, size_t bytes);
+template <typename... KArgs, typename... Args>
+furax_status launch_dyn(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                        Args... args)
+{
+    if (smem > 48 * 1024) {
+        furax_status rc = allow_smem((const void *)kern, smem);
+        if (rc) return rc;
+    }
+    kern<<<grid, block, smem, st>>>(args...);
+    return FURAX_OK;
+}
+
+struct CgWs;
+
+}  // namespace fx
+
+// Handles (opaque to the C API).
+struct furax_pointing {
+    int32_t mode = 0;
+    int32_t n_obs = 0;
+    std::vector<fx::ObsInfo> obs;     // host copy
+    fx::ObsInfo *d_obs = nullptr;
+    std::vector<fx::Tile> tiles;      // host copy
+    fx::Tile *d_tiles = nullptr;
+    int64_t n_tiles = 0;
+    std::vector<fx::PTile> ptiles;
+    fx::PTile *d_ptiles = nullptr;
+    int64_t n_ptiles = 0;
+    const double *q_bore = nullptr, *q_det = nullptr;
+    double2 *d_psi_cs = nullptr;
+    bool has_psi = false;
+    int32_t *pix = nullptr;
+    float *c32 = nullptr, *s32 = nullptr;
+    double *c64 = nullptr, *s64 = nullptr;
+    int64_t nsamp_total = 0, npix_total = 0, ndet_total = 0, nbore_total = 0, n_invalid = 0;
+    int32_t max_ndet = 0;
+    // workspaces, allocated on first use and freed by destroy
+    float4 *ws_map32 = nullptr;       // [npix] padded FP32 copy of a map for the gather
+    float4 *ws_acc_hi = nullptr;      // [npix] FP32 accumulator (I,Q,U,-)
+    float4 *ws_acc_lo = nullptr;      // [npix] FP32 compensation (KAHAN)
+    double *ws_acc64 = nullptr;       // [npix][3] FP64 accumulator
+    double *ws_x64 = nullptr;         // [npix][3] masked FP64 copy
+    void *ws_tod = nullptr;           // [nsamp] scratch TOD (FP64 size)
+    void *ws_tod2 = nullptr;
+    int32_t *ws_hits = nullptr;       // [npix] hit counts when the caller passes none
+    fx::CgWs *cg = nullptr;           // solver workspace (allocated by the first solve)
+    fx::PointingView view() const {
+        return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c64, s64};
+    }
+};
+
+struct furax_noise {
+    int32_t kind = 0;
+    int32_t ntaps = 0;
+    int64_t ndet_total = 0;
+    int64_t nsamp_total = 0;
+    double *p64 = nullptr;
+    float *p32 = nullptr;
+    double *diag = nullptr;
+    fx::ObsInfo *d_obs = nullptr;     // TOD layout for the standalone N^-1
+    fx::Tile *d_tiles = nullptr;
+    int64_t n_tiles = 0;
+    fx::NoiseView view() const { return fx::NoiseView{kind, ntaps, p64, p32, diag}; }
+};
+
+namespace fx {
+
+furax_status ensure_ws(furax_pointing *p, void **ptr, size_t bytes);
+
+// ---- launchers (pointing.cu)
+furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, float *s32, double *c64,
+                           double *s64, unsigned long long *n_invalid, cudaStream_t st, bool all_mode);
+furax_status launch_set_psi(furax_pointing *p, const double *psi, cudaStream_t st);
+furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void *tod, int tod_t, cudaStream_t st);
+furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void *map, int map_t, int acc,
+                       int32_t *hits, int accumulate, cudaStream_t st);
+furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rcond_min, double *blocks_inv,
+                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st);
+
+// ---- launchers (noise.cu)
+furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st);
+// Observation table, time tiles and pixel tiles of a batch.
+struct Layout {
+    std::vector<ObsInfo> obs;
+    std::vector<Tile> tiles;
+    std::vector<PTile> ptiles;
+    int64_t ndet = 0, nbore = 0, nsamp = 0, npix = 0;
+    int32_t max_ndet = 0;
+};
+void build_layout(const furax_obs_desc *d, Layout &L);
+furax_status prepare_kernels();
+// r_out = N^-1 (d - P m) in FP64 or FP32; also per-detector psi gradient partials
+furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, const void *d, int d_t,
+                              const double *m, double *chi2, double *grad_map, double *grad_psi, int precision,
+                              cudaStream_t st);
+
+// ---- launchers (fused.cu)
+// acc_* workspaces must be zeroed by the caller; x32 is the padded FP32 copy of the (masked) input.
+furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
+                              float4 *acc_hi, float4 *acc_lo, double *acc64, cudaStream_t st);
+furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, const double *x, double *acc64,
+                              cudaStream_t st);
+// b = P^T N^-1 d accumulated into acc64 (FP64 stencil)
+furax_status launch_rhs_f64(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *acc64,
+                            cudaStream_t st);
+
+// ---- vector helpers (solver.cu)
+furax_status launch_pack_x32(const furax_pointing *p, const double *x, const uint8_t *valid, float4 *x32,
+                             float4 *zero_a, float4 *zero_b, cudaStream_t st);
+furax_status launch_finalize_acc(const furax_pointing *p, int acc, const float4 *hi, const float4 *lo,
+                                 const double *acc64, const uint8_t *valid, double *out, cudaStream_t st);
+furax_status launch_mask_copy(const furax_pointing *p, const double *x, const uint8_t *valid, double *out,
+                              cudaStream_t st);
+furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const double *x, double *out,
+                        const uint8_t *valid, int precision, int acc, cudaStream_t st);
+furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *x,
+                         uint8_t *valid, const furax_cg_opts *o, furax_cg_result *res, cudaStream_t st);
+
+}  // namespace fx

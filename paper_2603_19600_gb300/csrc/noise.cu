@@ -1,0 +1,195 @@
+// Standalone noise weighting N^-1 (HomothetyOperator / SymmetricBandToeplitzOperator,
+// Table 2 of the Furax paper) and chi^2 = (d - P m)^T N^-1 (d - P m) with its gradients
+// with respect to the map and the per-detector polarisation-angle offsets (the paper's
+// differentiability, "Summary"). Same tile skeleton as the fused operator.
+#include "tile.cuh"
+
+namespace fx {
+
+// ------------------------------------------------------------------------------------
+// Standalone N^-1 on a TOD (white or banded), FP32 or FP64.
+// ------------------------------------------------------------------------------------
+template <typename T, bool BANDED>
+__global__ void __launch_bounds__(FT) ninv_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                  NoiseView nv, const T *__restrict__ in, T *__restrict__ out)
+{
+    __shared__ T xs[BANDED ? XS : 1];
+    __shared__ T taps[MAXTAPS];
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    const int64_t row = ob.tod_off + tl.det * ob.nsamp;
+    if constexpr (!BANDED) {
+        const T w = white_scale<T>(nv, gdet);
+        for (int k = threadIdx.x; k < tl.len; k += FT) out[row + tl.t0 + k] = in[row + tl.t0 + k] * w;
+        return;
+    } else {
+        load_taps<T>(nv, gdet, taps);
+        const int nload = tl.len + 2 * kHalo;
+        for (int u = threadIdx.x; u < nload; u += FT) {
+            const int64_t t = tl.t0 - kHalo + u;
+            xs[spos(u)] = (t >= 0 && t < ob.nsamp) ? in[row + t] : T(0);
+        }
+        __syncthreads();
+        const int base = threadIdx.x * FR;
+        if (base >= tl.len) return;
+        T y[FR];
+        band_product<T, FR>(xs, taps, base, y);
+#pragma unroll
+        for (int r = 0; r < FR; ++r)
+            if (base + r < tl.len) out[row + tl.t0 + base + r] = y[r];
+    }
+}
+
+furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st)
+{
+    if (n->n_tiles == 0) return FURAX_OK;
+    const unsigned g = (unsigned)n->n_tiles;
+    const NoiseView nv = n->view();
+    const bool b = n->kind == FURAX_NOISE_BANDED;
+    if (dtype == FURAX_F64) {
+        if (b) ninv_kernel<double, true><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, nv, (const double *)in, (double *)out);
+        else ninv_kernel<double, false><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, nv, (const double *)in, (double *)out);
+    } else {
+        if (b) ninv_kernel<float, true><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, nv, (const float *)in, (float *)out);
+        else ninv_kernel<float, false><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, nv, (const float *)in, (float *)out);
+    }
+    count_launches(1);
+    return check_launch("N^-1 apply");
+}
+
+// ------------------------------------------------------------------------------------
+// chi^2 = r^T N^-1 r, r = d - P m; grad_map -= 2 P^T N^-1 r; grad_psi -= 2 sum (N^-1 r) 2 (U c - Q s).
+// T is the precision of r and N^-1 r; all sums are FP64.
+// ------------------------------------------------------------------------------------
+template <int MODE, typename T, bool BANDED, typename DT>
+__global__ void __launch_bounds__(FT) chi2_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+                                                  const DT *__restrict__ d, const double *__restrict__ m,
+                                                  double *__restrict__ chi2, double *__restrict__ grad_map,
+                                                  double *__restrict__ grad_psi)
+{
+    extern __shared__ double csm[];
+    double *red = csm;                         // [2][FT/32]
+    T *xs = reinterpret_cast<T *>(red + 2 * (FT / 32));   // [XS]
+    T *taps = xs + XS;                         // [MAXTAPS]
+    T *sc = taps + MAXTAPS;                    // [CS]
+    T *ss = sc + CS;                           // [CS]
+    int32_t *spix = reinterpret_cast<int32_t *>(ss + CS);   // [CS]
+
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    const int64_t row = ob.tod_off + tl.det * ob.nsamp;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if constexpr (BANDED) load_taps<T>(nv, gdet, taps);
+    const int nload = tl.len + 2 * halo;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tl.t0 - halo + u;
+        T v = T(0), c = T(0), s = T(0);
+        int32_t pix = -1;
+        if (t >= 0 && t < ob.nsamp) {
+            pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
+            T model = T(0);
+            if (pix >= 0) {
+                const double *mm = m + 3 * (ob.map_off + pix);
+                model = (T)mm[0] + (T)mm[1] * c + (T)mm[2] * s;
+            }
+            v = (T)d[row + t] - model;
+        }
+        xs[spos(u)] = v;
+        const int core = u - halo;
+        if (core >= 0 && core < tl.len) { spix[spos(core)] = pix; sc[spos(core)] = c; ss[spos(core)] = s; }
+    }
+    __syncthreads();
+
+    double part_chi2 = 0.0, part_psi = 0.0;
+    const int base = threadIdx.x * FR;
+    if (base < tl.len) {
+        T y[FR];
+        if constexpr (BANDED) {
+            band_product<T, FR>(xs, taps, base, y);
+        } else {
+            const T w = white_scale<T>(nv, gdet);
+#pragma unroll
+            for (int r = 0; r < FR; ++r) y[r] = xs[spos(base + r)] * w;
+        }
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            const int k = base + r;
+            if (k >= tl.len) break;
+            const double nr = (double)y[r];
+            part_chi2 += (double)xs[spos(k + halo)] * nr;
+            const int32_t pix = spix[spos(k)];
+            if (pix < 0) continue;
+            const double c = (double)sc[spos(k)], s = (double)ss[spos(k)];
+            const int64_t gp = ob.map_off + pix;
+            const double *mm = m + 3 * gp;
+            part_psi += nr * 2.0 * (mm[2] * c - mm[1] * s);
+            if (grad_map) {
+                red_add_f64(grad_map + 3 * gp + 0, -2.0 * nr);
+                red_add_f64(grad_map + 3 * gp + 1, -2.0 * nr * c);
+                red_add_f64(grad_map + 3 * gp + 2, -2.0 * nr * s);
+            }
+        }
+    }
+    // block reduction (fixed order within the block)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        part_chi2 += __shfl_down_sync(0xffffffffu, part_chi2, o);
+        part_psi += __shfl_down_sync(0xffffffffu, part_psi, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = part_chi2; red[FT / 32 + (threadIdx.x >> 5)] = part_psi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < FT / 32; ++w) { a += red[w]; b += red[FT / 32 + w]; }
+        red_add_f64(chi2 + tl.obs, a);
+        if (grad_psi) red_add_f64(grad_psi + gdet, -2.0 * b);
+    }
+}
+
+template <int MODE, typename T, typename DT>
+static furax_status dispatch_chi2_t(const furax_pointing *p, const furax_noise *n, const DT *d, const double *m,
+                                    double *chi2, double *gm, double *gp, cudaStream_t st)
+{
+    const unsigned g = (unsigned)p->n_tiles;
+    const size_t smem = sizeof(double) * 2 * (FT / 32) + sizeof(T) * (XS + MAXTAPS + 2 * CS) + sizeof(int32_t) * CS;
+    if (n->kind == FURAX_NOISE_BANDED)
+        return launch_dyn(chi2_kernel<MODE, T, true, DT>, g, FT, smem, st, p->d_tiles, p->view(), n->view(), d, m, chi2,
+                          gm, gp);
+    return launch_dyn(chi2_kernel<MODE, T, false, DT>, g, FT, smem, st, p->d_tiles, p->view(), n->view(), d, m, chi2, gm,
+                      gp);
+}
+
+template <int MODE>
+static furax_status dispatch_chi2(const furax_pointing *p, const furax_noise *n, const void *d, int d_t,
+                                  const double *m, double *chi2, double *gm, double *gp, int precision, cudaStream_t st)
+{
+    if (precision == FURAX_F64) {
+        if (d_t == FURAX_F64) return dispatch_chi2_t<MODE, double, double>(p, n, (const double *)d, m, chi2, gm, gp, st);
+        return dispatch_chi2_t<MODE, double, float>(p, n, (const float *)d, m, chi2, gm, gp, st);
+    }
+    if (d_t == FURAX_F64) return dispatch_chi2_t<MODE, float, double>(p, n, (const double *)d, m, chi2, gm, gp, st);
+    return dispatch_chi2_t<MODE, float, float>(p, n, (const float *)d, m, chi2, gm, gp, st);
+}
+
+furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, const double *m,
+                              double *chi2, double *grad_map, double *grad_psi, int precision, cudaStream_t st)
+{
+    furax_status rc;
+    if ((rc = check_cuda(cudaMemsetAsync(chi2, 0, sizeof(double) * p->n_obs, st), "memset"))) return rc;
+    if (grad_map && (rc = check_cuda(cudaMemsetAsync(grad_map, 0, sizeof(double) * 3 * p->npix_total, st), "memset")))
+        return rc;
+    if (grad_psi && (rc = check_cuda(cudaMemsetAsync(grad_psi, 0, sizeof(double) * p->ndet_total, st), "memset")))
+        return rc;
+    if (p->n_tiles == 0) return FURAX_OK;
+    if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_chi2<0>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
+    else if (p->mode == FURAX_POINTING_CACHE_F32)
+        rc = dispatch_chi2<1>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
+    else rc = dispatch_chi2<2>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
+    if (rc) return rc;
+    count_launches(1);
+    return check_launch("chi2 and gradients");
+}
+
+}  // namespace fx

@@ -1,0 +1,332 @@
+// Pointing operator kernels: expansion (pixel + weights), P (gather), P^T (scatter-add)
+// and the block-Jacobi preconditioner (Furax paper: PointingOperator, Table 3 and
+// "Map-making classes"; transpose, Table 1; BJPreconditioner).
+//
+// Work is cut into tiles of one detector x up to TILE consecutive samples, listed per
+// observation, so one launch covers a whole batch of ragged observations.
+#include "internal.cuh"
+#include "pointing_math.cuh"
+#include "atomics.cuh"
+
+namespace fx {
+
+// ------------------------------------------------------------------------------------
+// Expansion: pixel and weights for every sample (FP64 recipe), cached or returned.
+// ------------------------------------------------------------------------------------
+template <typename WT>
+__global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                     const double *__restrict__ q_bore, const double *__restrict__ q_det,
+                                                     const double2 *__restrict__ psi_cs, int32_t *__restrict__ pix_out,
+                                                     WT *__restrict__ c_out, WT *__restrict__ s_out,
+                                                     unsigned long long *__restrict__ n_invalid)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    const Quat qd = load_quat(q_det, gdet);
+    const double2 cs = psi_cs ? psi_cs[gdet] : make_double2(1.0, 0.0);
+    int bad = 0;
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int64_t t = tl.t0 + k;
+        SampleF64 r = point_f64(load_quat(q_bore, ob.bore_off + t), qd, ob.nside);
+        double c = r.c, s = r.s;
+        if (psi_cs && r.pix >= 0) rotate_psi<double>(c, s, cs);
+        const int64_t i = ob.tod_off + tl.det * ob.nsamp + t;
+        pix_out[i] = r.pix;
+        if (c_out) { c_out[i] = (WT)c; s_out[i] = (WT)s; }
+        bad += (r.pix < 0);
+    }
+    if (n_invalid) {
+        bad = __reduce_add_sync(0xffffffffu, bad);
+        if ((threadIdx.x & 31) == 0 && bad) atomicAdd(n_invalid, (unsigned long long)bad);
+    }
+}
+
+furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, float *s32, double *c64, double *s64,
+                           unsigned long long *n_invalid, cudaStream_t st, bool)
+{
+    if (p->n_tiles == 0) return FURAX_OK;
+    const double2 *cs = p->has_psi ? p->d_psi_cs : nullptr;
+    if (c64 || (!c32 && !c64))
+        expand_kernel<double><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
+                                                                    c64, s64, n_invalid);
+    else
+        expand_kernel<float><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
+                                                                   c32, s32, n_invalid);
+    count_launches(1);
+    return check_launch("pointing expansion");
+}
+
+__global__ void psi_kernel(const double *__restrict__ psi, double2 *__restrict__ cs, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        double s, c;
+        sincos(2.0 * psi[i], &s, &c);
+        cs[i] = make_double2(c, s);
+    }
+}
+
+furax_status launch_set_psi(furax_pointing *p, const double *psi, cudaStream_t st)
+{
+    if (!psi) { p->has_psi = false; return FURAX_OK; }
+    int64_t n = p->ndet_total;
+    psi_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, p->d_psi_cs, n);
+    count_launches(1);
+    p->has_psi = true;
+    return check_launch("psi offsets");
+}
+
+// ------------------------------------------------------------------------------------
+// P: tod = I + Q c + U s
+// ------------------------------------------------------------------------------------
+template <int MODE, typename T, typename MT, typename TT>
+__global__ void __launch_bounds__(256) P_kernel(const Tile *__restrict__ tiles, PointingView pv,
+                                                const MT *__restrict__ map, TT *__restrict__ tod)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tl.obs];
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int64_t t = tl.t0 + k;
+        T c, s;
+        const int32_t pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
+        T v = (T)0;
+        if (pix >= 0) {
+            const MT *m = map + 3 * (ob.map_off + pix);
+            v = (T)m[0] + (T)m[1] * c + (T)m[2] * s;
+        }
+        tod[ob.tod_off + tl.det * ob.nsamp + t] = (TT)v;
+    }
+}
+
+template <int MODE>
+static void dispatch_P(const furax_pointing *p, const void *map, int map_t, void *tod, int tod_t, cudaStream_t st)
+{
+    const unsigned g = (unsigned)p->n_tiles;
+    const PointingView pv = p->view();
+    if (map_t == FURAX_F64 && tod_t == FURAX_F64)
+        P_kernel<MODE, double, double, double><<<g, 256, 0, st>>>(p->d_tiles, pv, (const double *)map, (double *)tod);
+    else if (map_t == FURAX_F64)
+        P_kernel<MODE, double, double, float><<<g, 256, 0, st>>>(p->d_tiles, pv, (const double *)map, (float *)tod);
+    else if (tod_t == FURAX_F64)
+        P_kernel<MODE, double, float, double><<<g, 256, 0, st>>>(p->d_tiles, pv, (const float *)map, (double *)tod);
+    else
+        P_kernel<MODE, float, float, float><<<g, 256, 0, st>>>(p->d_tiles, pv, (const float *)map, (float *)tod);
+}
+
+furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void *tod, int tod_t, cudaStream_t st)
+{
+    if (p->n_tiles == 0) return FURAX_OK;
+    if (p->mode == FURAX_POINTING_ON_THE_FLY) dispatch_P<0>(p, map, map_t, tod, tod_t, st);
+    else if (p->mode == FURAX_POINTING_CACHE_F32) dispatch_P<1>(p, map, map_t, tod, tod_t, st);
+    else dispatch_P<2>(p, map, map_t, tod, tod_t, st);
+    count_launches(1);
+    return check_launch("pointing apply");
+}
+
+// ------------------------------------------------------------------------------------
+// P^T: accumulate tod * (1, c, s) per pixel into a workspace, then finalise into the map.
+// ------------------------------------------------------------------------------------
+template <int MODE, int ACC, typename T, typename TT>
+__global__ void __launch_bounds__(256) PT_kernel(const Tile *__restrict__ tiles, PointingView pv,
+                                                 const TT *__restrict__ tod, float4 *__restrict__ hi,
+                                                 float4 *__restrict__ lo, double *__restrict__ acc64,
+                                                 int32_t *__restrict__ hits)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tl.obs];
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int64_t t = tl.t0 + k;
+        T c, s;
+        const int32_t pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
+        if (pix < 0) continue;
+        const int64_t gp = ob.map_off + pix;
+        const T y = (T)tod[ob.tod_off + tl.det * ob.nsamp + t];
+        if constexpr (ACC == FURAX_ACC_F64) {
+            red_add_f64(acc64 + 3 * gp + 0, (double)y);
+            red_add_f64(acc64 + 3 * gp + 1, (double)(y * c));
+            red_add_f64(acc64 + 3 * gp + 2, (double)(y * s));
+        } else if constexpr (ACC == FURAX_ACC_F32) {
+            red_add_v4(hi + gp, make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
+        } else {
+            kahan_add_v4(hi + gp, lo + gp, make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
+        }
+        if (hits) red_add_s32(hits + gp, 1);
+    }
+}
+
+// map (+)= accumulator, in the map's dtype.
+template <typename MT>
+__global__ void PT_finalize_kernel(int acc, const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                                   const double *__restrict__ acc64, MT *__restrict__ map, int64_t npix, int accumulate)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        double v0, v1, v2;
+        if (acc == FURAX_ACC_F64) { v0 = acc64[3 * p]; v1 = acc64[3 * p + 1]; v2 = acc64[3 * p + 2]; }
+        else {
+            float4 h = hi[p];
+            v0 = h.x; v1 = h.y; v2 = h.z;
+            if (acc == FURAX_ACC_F32_KAHAN) { float4 l = lo[p]; v0 += l.x; v1 += l.y; v2 += l.z; }
+        }
+        if (accumulate) { v0 += (double)map[3 * p]; v1 += (double)map[3 * p + 1]; v2 += (double)map[3 * p + 2]; }
+        map[3 * p] = (MT)v0; map[3 * p + 1] = (MT)v1; map[3 * p + 2] = (MT)v2;
+    }
+}
+
+template <int MODE, int ACC>
+static void dispatch_PT_acc(const furax_pointing *p, const void *tod, int tod_t, float4 *hi, float4 *lo, double *a64,
+                            int32_t *hits, cudaStream_t st)
+{
+    const unsigned g = (unsigned)p->n_tiles;
+    const PointingView pv = p->view();
+    if (tod_t == FURAX_F64)
+        PT_kernel<MODE, ACC, double, double><<<g, 256, 0, st>>>(p->d_tiles, pv, (const double *)tod, hi, lo, a64, hits);
+    else if (ACC == FURAX_ACC_F64)
+        PT_kernel<MODE, ACC, double, float><<<g, 256, 0, st>>>(p->d_tiles, pv, (const float *)tod, hi, lo, a64, hits);
+    else
+        PT_kernel<MODE, ACC, float, float><<<g, 256, 0, st>>>(p->d_tiles, pv, (const float *)tod, hi, lo, a64, hits);
+}
+
+template <int MODE>
+static void dispatch_PT(const furax_pointing *p, const void *tod, int tod_t, int acc, float4 *hi, float4 *lo,
+                        double *a64, int32_t *hits, cudaStream_t st)
+{
+    if (acc == FURAX_ACC_F64) dispatch_PT_acc<MODE, FURAX_ACC_F64>(p, tod, tod_t, hi, lo, a64, hits, st);
+    else if (acc == FURAX_ACC_F32) dispatch_PT_acc<MODE, FURAX_ACC_F32>(p, tod, tod_t, hi, lo, a64, hits, st);
+    else dispatch_PT_acc<MODE, FURAX_ACC_F32_KAHAN>(p, tod, tod_t, hi, lo, a64, hits, st);
+}
+
+furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void *map, int map_t, int acc,
+                       int32_t *hits, int accumulate, cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    const int64_t np = p->npix_total;
+    furax_status rc;
+    float4 *hi = nullptr, *lo = nullptr;
+    double *a64 = nullptr;
+    if (acc == FURAX_ACC_F64) {
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc64, sizeof(double) * 3 * np))) return rc;
+        a64 = pm->ws_acc64;
+        if ((rc = check_cuda(cudaMemsetAsync(a64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
+    } else {
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_hi, sizeof(float4) * np))) return rc;
+        hi = pm->ws_acc_hi;
+        if ((rc = check_cuda(cudaMemsetAsync(hi, 0, sizeof(float4) * np, st), "memset"))) return rc;
+        if (acc == FURAX_ACC_F32_KAHAN) {
+            if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_lo, sizeof(float4) * np))) return rc;
+            lo = pm->ws_acc_lo;
+            if ((rc = check_cuda(cudaMemsetAsync(lo, 0, sizeof(float4) * np, st), "memset"))) return rc;
+        }
+    }
+    if (hits && !accumulate)
+        if ((rc = check_cuda(cudaMemsetAsync(hits, 0, sizeof(int32_t) * np, st), "memset"))) return rc;
+    if (p->n_tiles > 0) {
+        if (p->mode == FURAX_POINTING_ON_THE_FLY) dispatch_PT<0>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
+        else if (p->mode == FURAX_POINTING_CACHE_F32) dispatch_PT<1>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
+        else dispatch_PT<2>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
+        count_launches(1);
+        if ((rc = check_launch("pointing transpose"))) return rc;
+    }
+    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 16);
+    if (map_t == FURAX_F64)
+        PT_finalize_kernel<double><<<fg, 256, 0, st>>>(acc, hi, lo, a64, (double *)map, np, accumulate);
+    else
+        PT_finalize_kernel<float><<<fg, 256, 0, st>>>(acc, hi, lo, a64, (float *)map, np, accumulate);
+    count_launches(1);
+    return check_launch("pointing transpose finalise");
+}
+
+// ------------------------------------------------------------------------------------
+// Block-Jacobi: M_p = sum ninv w w^T (6 unique entries), hits; then invert in FP64.
+// ------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) bj_accum_kernel(const Tile *__restrict__ tiles, PointingView pv,
+                                                       const double *__restrict__ ninv_diag, double *__restrict__ m6,
+                                                       int32_t *__restrict__ hits)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tl.obs];
+    const double w0 = ninv_diag[ob.det_off + tl.det];
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int64_t t = tl.t0 + k;
+        double c, s;
+        const int32_t pix = get_sample<MODE, double>(pv, ob, tl.det, t, c, s);
+        if (pix < 0) continue;
+        const int64_t gp = ob.map_off + pix;
+        double *m = m6 + 6 * gp;
+        const double wc = w0 * c, ws = w0 * s;
+        red_add_f64(m + 0, w0);
+        red_add_f64(m + 1, wc);
+        red_add_f64(m + 2, ws);
+        red_add_f64(m + 3, wc * c);
+        red_add_f64(m + 4, wc * s);
+        red_add_f64(m + 5, ws * s);
+        red_add_s32(hits + gp, 1);
+    }
+}
+
+__device__ __forceinline__ double norm1_sym(double a, double b, double c, double d, double e, double f)
+{
+    double c0 = fabs(a) + fabs(b) + fabs(c);
+    double c1 = fabs(b) + fabs(d) + fabs(e);
+    double c2 = fabs(c) + fabs(e) + fabs(f);
+    return fmax(c0, fmax(c1, c2));
+}
+
+// In place: m6 holds M on entry and M^-1 (0 where invalid) on exit.
+__global__ void bj_invert_kernel(double *__restrict__ m6, const int32_t *__restrict__ hits, uint8_t *__restrict__ valid,
+                                 double *__restrict__ rcond, int64_t npix, double rcond_min)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        double *m = m6 + 6 * p;
+        const double a = m[0], b = m[1], c = m[2], d = m[3], e = m[4], f = m[5];
+        // cofactors of [[a,b,c],[b,d,e],[c,e,f]]
+        const double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
+        const double D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
+        const double det = a * A + b * B + c * C;
+        bool ok = hits[p] >= 3 && det > 0.0;
+        double rc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+        if (ok) {
+            const double id = 1.0 / det;
+            v[0] = A * id; v[1] = B * id; v[2] = C * id; v[3] = D * id; v[4] = E * id; v[5] = F * id;
+            rc = 1.0 / (norm1_sym(a, b, c, d, e, f) * norm1_sym(v[0], v[1], v[2], v[3], v[4], v[5]));
+            ok = rc >= rcond_min;
+        }
+        for (int k = 0; k < 6; ++k) m[k] = ok ? v[k] : 0.0;
+        valid[p] = ok ? 1 : 0;
+        if (rcond) rcond[p] = rc;
+    }
+}
+
+furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rcond_min, double *blocks_inv,
+                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    const int64_t np = p->npix_total;
+    furax_status rc;
+    int32_t *h = hits;
+    if (!h) {
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_hits, sizeof(int32_t) * np))) return rc;
+        h = pm->ws_hits;
+    }
+    if ((rc = check_cuda(cudaMemsetAsync(blocks_inv, 0, sizeof(double) * 6 * np, st), "memset"))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(h, 0, sizeof(int32_t) * np, st), "memset"))) return rc;
+    if (p->n_tiles > 0) {
+        const unsigned g = (unsigned)p->n_tiles;
+        const PointingView pv = p->view();
+        if (p->mode == FURAX_POINTING_ON_THE_FLY)
+            bj_accum_kernel<0><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
+        else if (p->mode == FURAX_POINTING_CACHE_F32)
+            bj_accum_kernel<1><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
+        else
+            bj_accum_kernel<2><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
+        count_launches(1);
+        if ((rc = check_launch("preconditioner accumulation"))) return rc;
+    }
+    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 16);
+    bj_invert_kernel<<<fg, 256, 0, st>>>(blocks_inv, h, valid, rcond, np, rcond_min);
+    count_launches(1);
+    return check_launch("preconditioner inversion");
+}
+
+}  // namespace fx

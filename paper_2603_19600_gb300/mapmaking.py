@@ -1,0 +1,237 @@
+"""Map-making on GB300: pointing P, noise weighting N^-1, block-Jacobi, PCG, chi^2 gradients.
+
+Thin object layer over the C ABI (``_native``): it allocates outputs with torch and
+passes pointers; every computation runs in libfurax's CUDA kernels. Names follow the
+paper's operators (Furax, arXiv 2603.19600): PointingOperator (P), its transpose,
+HomothetyOperator / SymmetricBandToeplitzOperator (N^-1), BJPreconditioner, and the
+maximum-likelihood estimator (P^T N^-1 P)^-1 P^T N^-1 d solved by PCG.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _native as nat
+
+_MODES = {"on_the_fly": nat.FURAX_POINTING_ON_THE_FLY, "cache_f32": nat.FURAX_POINTING_CACHE_F32,
+          "cache_f64": nat.FURAX_POINTING_CACHE_F64}
+_ACC = {"f64": nat.FURAX_ACC_F64, "f32_kahan": nat.FURAX_ACC_F32_KAHAN, "f32": nat.FURAX_ACC_F32}
+_PREC = {"f32": nat.FURAX_F32, "f64": nat.FURAX_F64}
+
+
+class Pointing:
+    """Pointing operator of a batch of observations (one map per observation).
+
+    q_bore: float64 [sum nsamp][4] (w, x, y, z); q_det: float64 [sum ndet][4]; both on the GPU
+    and kept alive by this object. mode: "cache_f32" (pixel + FP32 weights cached, 12 B/sample),
+    "cache_f64" (20 B/sample) or "on_the_fly" (recomputed from the quaternions each call).
+    """
+
+    def __init__(self, q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode="cache_f32", stream=None):
+        self.ndet, self.nsamp, self.nside = [list(map(int, v)) for v in (ndet, nsamp, nside)]
+        self.q_bore = q_bore.contiguous()
+        self.q_det = q_det.contiguous()
+        self.mode = mode
+        self.handle = None
+        self.handle = nat.furax_pointing_create(self.q_bore, self.q_det, self.ndet, self.nsamp, self.nside,
+                                                psi_offset, _MODES[mode], stream)
+        info = nat.furax_pointing_info(self.handle)
+        self.nsamp_total = info["nsamp_total"]
+        self.npix_total = info["npix_total"]
+        self.ndet_total = info["ndet_total"]
+        self.n_invalid = info["n_invalid"]
+        self.device = self.q_bore.device
+
+    @classmethod
+    def from_observations(cls, observations, mode="cache_f32", device="cuda", stream=None):
+        """Build from objects with .q_bore, .q_det (numpy) and .nside (see the synth module)."""
+        qb = torch.cat([torch.as_tensor(o.q_bore) for o in observations]).to(device, torch.float64)
+        qd = torch.cat([torch.as_tensor(o.q_det) for o in observations]).to(device, torch.float64)
+        psi = None
+        if any(getattr(o, "psi_offset", None) is not None for o in observations):
+            psi = torch.cat([torch.as_tensor(o.psi_offset if o.psi_offset is not None else [0.0] * o.ndet)
+                             for o in observations]).to(device, torch.float64)
+        return cls(qb, qd, [o.q_det.shape[0] for o in observations], [o.q_bore.shape[0] for o in observations],
+                   [o.nside for o in observations], psi, mode, stream)
+
+    def close(self):
+        if self.handle:
+            nat.furax_pointing_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refresh(self):
+        """Recompute the cached pointing from the (possibly updated) quaternion tensors."""
+        nat.furax_pointing_refresh(self.handle)
+
+    def set_psi_offset(self, psi_offset):
+        nat.furax_pointing_set_psi_offset(self.handle, None if psi_offset is None else psi_offset.contiguous())
+
+    def expand(self, dtype=torch.float64):
+        """Per-sample pixel (int32, local to its observation) and weights cos 2psi, sin 2psi."""
+        pix = torch.empty(self.nsamp_total, dtype=torch.int32, device=self.device)
+        c = torch.empty(self.nsamp_total, dtype=dtype, device=self.device)
+        s = torch.empty_like(c)
+        nat.furax_pointing_expand(self.handle, pix, c, s)
+        return pix, c, s
+
+    def apply(self, m, out=None, dtype=None):
+        """tod = P m; m: [npix_total][3]."""
+        if out is None:
+            out = torch.empty(self.nsamp_total, dtype=dtype or m.dtype, device=self.device)
+        nat.furax_pointing_apply(self.handle, m.contiguous(), out)
+        return out
+
+    def transpose(self, tod, out=None, acc="f64", hits=False, dtype=torch.float64, accumulate=False):
+        """map = P^T tod (and hit counts when hits=True)."""
+        if out is None:
+            out = torch.zeros(self.npix_total, 3, dtype=dtype, device=self.device)
+        h = torch.zeros(self.npix_total, dtype=torch.int32, device=self.device) if hits else None
+        nat.furax_pointing_transpose(self.handle, tod.contiguous(), out, _ACC[acc], h, accumulate)
+        return (out, h) if hits else out
+
+
+class Noise:
+    """Inverse noise covariance per detector: white (variances) or a symmetric band (taps)."""
+
+    def __init__(self, pointing: Pointing, kind: str, params: torch.Tensor, stream=None):
+        self.kind = kind
+        p = params.to(pointing.device, torch.float64).contiguous()
+        if kind == "white":
+            self.ntaps = 1
+            h = nat.furax_noise_create(nat.FURAX_NOISE_WHITE, p.reshape(-1), 1, pointing.ndet, pointing.nsamp,
+                                       pointing.nside, stream)
+        elif kind == "banded":
+            p = p.reshape(pointing.ndet_total, -1)
+            self.ntaps = p.shape[1]
+            h = nat.furax_noise_create(nat.FURAX_NOISE_BANDED, p, self.ntaps, pointing.ndet, pointing.nsamp,
+                                       pointing.nside, stream)
+        else:
+            raise ValueError(f"unknown noise kind {kind}")
+        self.handle = h
+        self.params = p
+
+    @classmethod
+    def white(cls, pointing, sigma2):
+        return cls(pointing, "white", torch.as_tensor(sigma2))
+
+    @classmethod
+    def banded(cls, pointing, taps):
+        return cls(pointing, "banded", torch.as_tensor(taps))
+
+    def close(self):
+        if self.handle:
+            nat.furax_noise_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def inv_apply(self, x, out=None):
+        if out is None:
+            out = torch.empty_like(x)
+        nat.furax_noise_inv_apply(self.handle, x.contiguous(), out)
+        return out
+
+
+def blockdiag_precond(P: Pointing, N: Noise, rcond_min=1e-3):
+    inv = torch.empty(P.npix_total, 6, dtype=torch.float64, device=P.device)
+    valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
+    hits = torch.empty(P.npix_total, dtype=torch.int32, device=P.device)
+    rcond = torch.empty(P.npix_total, dtype=torch.float64, device=P.device)
+    nat.furax_blockdiag_precond(P.handle, N.handle, rcond_min, inv, valid, hits, rcond)
+    return dict(inv=inv, valid=valid.bool(), valid_u8=valid, hits=hits, rcond=rcond)
+
+
+def ptnp_apply(P: Pointing, N: Noise, x, valid=None, precision="f32", acc="f32", out=None):
+    """out = S P^T N^-1 P S^T x (x float64 [npix_total][3])."""
+    if out is None:
+        out = torch.empty_like(x)
+    v = None if valid is None else valid.to(torch.uint8).contiguous()
+    nat.furax_ptnp_apply(P.handle, N.handle, x.contiguous(), out, v, _PREC[precision], _ACC[acc])
+    return out
+
+
+def rhs(P: Pointing, N: Noise, d, valid=None):
+    b = torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device)
+    v = None if valid is None else valid.to(torch.uint8).contiguous()
+    nat.furax_rhs(P.handle, N.handle, d.contiguous(), b, v)
+    return b
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    outer: int
+    rel_res: float
+    true_rel_res: float
+    n_valid: int
+    history: list = field(default_factory=list)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == nat.FURAX_OK
+
+
+def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64", acc="f32", inner_tol=1e-5,
+                max_outer=8, use_graph=True, check_every=10, rcond_min=1e-3, binned_only=False, hist_len=None,
+                out=None, true_residual=True):
+    """Solve the map-making normal equations per observation; returns (map, valid mask, SolveInfo)."""
+    o = nat.default_cg_opts()
+    o.maxiter, o.tol, o.precision, o.acc = int(maxiter), float(tol), _PREC[precision], _ACC[acc]
+    o.inner_tol, o.max_outer, o.use_graph = float(inner_tol), int(max_outer), int(bool(use_graph))
+    o.check_every, o.rcond_min, o.binned_only = int(check_every), float(rcond_min), int(bool(binned_only))
+    o.true_residual = int(bool(true_residual))
+    x = out if out is not None else torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device)
+    valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
+    rc, res, hist = nat.furax_mapmaker_cg(P.handle, N.handle, d.contiguous(), x, valid, o,
+                                          hist_len if hist_len is not None else maxiter + 1)
+    return x, valid.bool(), SolveInfo(rc, res.iters, res.outer, res.rel_res, res.true_rel_res, res.n_valid, hist)
+
+
+def chi2_grad(P: Pointing, N: Noise, d, m, precision="f64", want_map=True, want_psi=True):
+    """chi^2 per observation, d chi^2/d m [npix_total][3] and d chi^2/d psi_det [ndet_total]."""
+    chi2 = torch.empty(len(P.ndet), dtype=torch.float64, device=P.device)
+    gm = torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device) if want_map else None
+    gp = torch.empty(P.ndet_total, dtype=torch.float64, device=P.device) if want_psi else None
+    nat.furax_chi2_grad(P.handle, N.handle, d.contiguous(), m.contiguous(), chi2, gm, gp, _PREC[precision])
+    return chi2, gm, gp
+
+
+class Chi2(torch.autograd.Function):
+    """chi^2(m, delta) = (d - P(delta) m)^T N^-1 (d - P(delta) m), summed over observations.
+
+    forward(m, psi_offset, P, N, d, precision) -> scalar; the backward is the hand-written
+    gradient pair d chi^2/d m = -2 P^T N^-1 r and d chi^2/d delta_j = -2 sum_t (N^-1 r) 2 (U c - Q s),
+    computed by one fused kernel in the forward pass and scaled by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, m, psi_offset, P: Pointing, N: Noise, d, precision="f64"):
+        P.set_psi_offset(psi_offset.detach().to(torch.float64).contiguous())
+        chi2, gm, gp = chi2_grad(P, N, d, m.detach().to(torch.float64), precision,
+                                 want_map=ctx.needs_input_grad[0], want_psi=ctx.needs_input_grad[1])
+        ctx.save_for_backward(*(t for t in (gm, gp) if t is not None))
+        ctx.has = (gm is not None, gp is not None)
+        return chi2.sum().to(m.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        saved = list(ctx.saved_tensors)
+        gm = saved.pop(0) * g if ctx.has[0] else None
+        gp = saved.pop(0) * g if ctx.has[1] else None
+        return gm, gp, None, None, None, None
+
+
+def chi2(m, psi_offset, P: Pointing, N: Noise, d, precision="f64"):
+    return Chi2.apply(m, psi_offset, P, N, d, precision)

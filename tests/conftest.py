@@ -18,3 +18,21 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def fx():
+    """The CUDA library through its Python binding (skips without a GPU)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_19600_gb300 import build
+    build.build()
+    import paper_2603_19600_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="session")
+def dev(fx):
+    import torch
+    return torch.device("cuda:0")

@@ -1,0 +1,157 @@
+"""GPU map-making vs the FP64 oracle: binned map, FP64 PCG, mixed-precision PCG with defect
+correction to a true residual of 1e-8, per-observation batched solves, graph vs eager."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def c1(orc):
+    obs, sky, noise, sigma2 = synth.config1()
+    pix, c, s, _ = orc.pointing(obs.nside, obs.q_bore, obs.q_det)
+    d = orc.P(pix, c, s, sky) + noise
+    nz = orc.Noise(sigma2=sigma2)
+    bj = orc.bj(obs.npix, pix, c, s, nz)
+    b = orc.rhs(obs.npix, pix, c, s, nz, bj["valid"], d)
+    return obs, sky, d, sigma2, pix, c, s, nz, bj, b
+
+
+def test_c1_binned_and_pcg_fp64(fx, dev, orc, c1):
+    obs, sky, d, sigma2, pix, c, s, nz, bj, b = c1
+    P = fx.Pointing.from_observations([obs], mode="cache_f64", device=dev)
+    N = fx.Noise.white(P, sigma2)
+    dt = torch.as_tensor(d.ravel(), device=dev)
+    v = bj["valid"]
+    xb, valid, info = fx.mapmaker_cg(P, N, dt, binned_only=True)
+    assert np.array_equal(valid.cpu().numpy(), v)
+    ref_binned = orc.binned_map(bj, b)
+    assert rel(xb.cpu().numpy()[v], ref_binned[v]) < 1e-10
+    x, valid, info = fx.mapmaker_cg(P, N, dt, maxiter=30, tol=1e-8, precision="f64")
+    ox, it, hist = orc.pcg(obs.npix, pix, c, s, nz, v, bj["inv"], b, 30, 1e-8)
+    assert info.converged and info.iters == it == 1   # white noise: one step to the binned map
+    assert rel(x.cpu().numpy()[v], ox[v]) < 1e-10
+    assert np.all(x.cpu().numpy()[~v] == 0)
+    assert info.true_rel_res < 1e-12
+    assert info.n_valid == v.sum()
+
+
+@pytest.fixture(scope="module")
+def banded(orc):
+    """Reduced config-2 geometry: nside 64, 32 hex detectors x 16384 samples, 1/f noise."""
+    o = synth.Observation(64, synth.satellite_scan(16384, t0=50.0), synth.hex_focal_plane(32))
+    pix, c, s, _ = orc.pointing(o.nside, o.q_bore, o.q_det)
+    sky = synth.gaussian_sky(o.nside, synth.rng(2, 0))
+    d = (orc.P(pix, c, s, sky) + synth.one_over_f_noise(32, 16384, synth.rng(2, 1))).astype(np.float32)
+    taps = np.tile(synth.inverse_noise_taps(), (32, 1))
+    nz = orc.Noise(taps=taps)
+    bj = orc.bj(o.npix, pix, c, s, nz)
+    b = orc.rhs(o.npix, pix, c, s, nz, bj["valid"], d.astype(np.float64))
+    return o, sky, d, taps, pix, c, s, nz, bj, b
+
+
+def test_banded_pcg_fp64_matches_oracle_iterates(fx, dev, orc, banded):
+    o, sky, d, taps, pix, c, s, nz, bj, b = banded
+    P = fx.Pointing.from_observations([o], mode="cache_f64", device=dev)
+    N = fx.Noise.banded(P, taps)
+    v = bj["valid"]
+    dt = torch.as_tensor(d.ravel(), device=dev)
+    for k in (1, 5, 20):
+        x, valid, info = fx.mapmaker_cg(P, N, dt, maxiter=k, tol=0.0, precision="f64", check_every=5)
+        ox, it, hist = orc.pcg(o.npix, pix, c, s, nz, v, bj["inv"], b, k, 0.0)
+        assert info.iters == it == k
+        assert rel(x.cpu().numpy()[v], ox[v]) < 1e-9, k
+        np.testing.assert_allclose(info.history[1:], hist[1:], rtol=1e-7)
+
+
+def test_banded_pcg_converges_fp64_and_mixed(fx, dev, orc, banded):
+    o, sky, d, taps, pix, c, s, nz, bj, b = banded
+    v = bj["valid"]
+    ox, it, hist = orc.pcg(o.npix, pix, c, s, nz, v, bj["inv"], b, 2000, 1e-12)
+    dt = torch.as_tensor(d.ravel(), device=dev)
+    P64 = fx.Pointing.from_observations([o], mode="cache_f64", device=dev)
+    x64, _, i64 = fx.mapmaker_cg(P64, fx.Noise.banded(P64, taps), dt, maxiter=2000, tol=1e-8, precision="f64")
+    assert i64.converged and i64.true_rel_res <= 1.5e-8
+    P32 = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    for acc in ("f32", "f32_kahan", "f64"):
+        x32, _, i32 = fx.mapmaker_cg(P32, fx.Noise.banded(P32, taps), dt, maxiter=2000, tol=1e-8, precision="f32",
+                                     acc=acc, inner_tol=1e-5)
+        assert i32.converged, (acc, i32)
+        assert i32.true_rel_res <= 1e-8
+        assert i32.outer >= 1
+        # the FP32 cache holds rounded weights: the mixed solve converges to the same FP64 system
+        # only up to that rounding, so compare against the solution at the solver's tolerance
+        assert rel(x32.cpu().numpy()[v], ox[v]) < 1e-5, acc
+    assert rel(x64.cpu().numpy()[v], ox[v]) < 1e-6
+
+
+def test_noiseless_recovery_mixed(fx, dev, orc, banded):
+    o, sky, d, taps, pix, c, s, nz, bj, b = banded
+    v = bj["valid"]
+    m = sky.copy()
+    m[~v] = 0.0
+    P = fx.Pointing.from_observations([o], mode="cache_f64", device=dev)
+    N = fx.Noise.banded(P, taps)
+    dn = P.apply(torch.as_tensor(m, device=dev), dtype=torch.float64)
+    x, valid, info = fx.mapmaker_cg(P, N, dn, maxiter=3000, tol=1e-12, precision="f64")
+    assert rel(x.cpu().numpy()[v], m[v]) < 1e-10
+
+
+def test_graph_and_eager_identical(fx, dev, banded):
+    o, sky, d, taps, *_ = banded
+    P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    N = fx.Noise.banded(P, taps)
+    dt = torch.as_tensor(d.ravel(), device=dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xg, _, ig = fx.mapmaker_cg(P, N, dt, maxiter=30, tol=0.0, precision="f64", use_graph=True, check_every=10)
+        xe, _, ie = fx.mapmaker_cg(P, N, dt, maxiter=30, tol=0.0, precision="f64", use_graph=False, check_every=7)
+    s.synchronize()
+    assert ig.iters == ie.iters == 30
+    assert torch.equal(xg, xe)   # deterministic reductions, same launch sequence
+
+
+def test_batched_observations_solved_independently(fx, dev, orc):
+    """Ragged batch (per-observation nside, ndet, nsamp): each observation's PCG equals the oracle's."""
+    shapes = [(16, 4, 6000), (32, 9, 4097), (16, 12, 9000), (64, 5, 12000)]
+    obs = [synth.Observation(ns, synth.satellite_scan(n, t0=300.0 * i), synth.hex_focal_plane(nd))
+           for i, (ns, nd, n) in enumerate(shapes)]
+    taps_all, d_all, refs = [], [], []
+    for i, o in enumerate(obs):
+        pix, c, s, _ = orc.pointing(o.nside, o.q_bore, o.q_det)
+        taps = np.tile(synth.inverse_noise_taps(), (o.ndet, 1))
+        nz = orc.Noise(taps=taps)
+        sky = synth.gaussian_sky(o.nside, synth.rng(4, 10 + i))
+        d = orc.P(pix, c, s, sky) + synth.one_over_f_noise(o.ndet, o.nsamp, synth.rng(4, 20 + i))
+        bj = orc.bj(o.npix, pix, c, s, nz)
+        b = orc.rhs(o.npix, pix, c, s, nz, bj["valid"], d)
+        ox, it, _ = orc.pcg(o.npix, pix, c, s, nz, bj["valid"], bj["inv"], b, 15, 0.0)
+        refs.append((ox, bj["valid"]))
+        taps_all.append(taps)
+        d_all.append(d.ravel())
+    P = fx.Pointing.from_observations(obs, mode="cache_f64", device=dev)
+    N = fx.Noise.banded(P, np.concatenate(taps_all))
+    x, valid, info = fx.mapmaker_cg(P, N, torch.as_tensor(np.concatenate(d_all), device=dev), maxiter=15, tol=0.0,
+                                    precision="f64")
+    x = x.cpu().numpy()
+    valid = valid.cpu().numpy()
+    off = 0
+    for o, (ox, v) in zip(obs, refs):
+        assert np.array_equal(valid[off:off + o.npix], v)
+        assert rel(x[off:off + o.npix][v], ox[v]) < 1e-9
+        off += o.npix
+
+
+def test_maxiter_cap_reports_not_converged(fx, dev, banded):
+    o, sky, d, taps, *_ = banded
+    P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    x, _, info = fx.mapmaker_cg(P, fx.Noise.banded(P, taps), torch.as_tensor(d.ravel(), device=dev), maxiter=3,
+                                tol=1e-12, precision="f64")
+    assert not info.converged and info.iters == 3

@@ -310,3 +310,13 @@ def test_nonfinite_quaternion_gives_invalid_pixel(orc):
     assert bad == 4
     assert np.all(pix[:, [5, 9]] == -1)
     assert np.all(c[:, [5, 9]] == 0) and np.all(s[:, [5, 9]] == 0)
+
+
+def test_far_from_unit_quaternion_never_leaves_the_map(orc):
+    """Quaternions of norm up to 3 can push the cap formula past the last ring; such samples
+    get pixel -1, every other pixel stays inside the map."""
+    qb = synth.satellite_scan(20000) * np.linspace(0.3, 3.0, 20000)[:, None]
+    pix, c, s, bad = orc.pointing(64, qb, synth.copointed_detectors([0.0, 45.0]))
+    assert np.all((pix == -1) | ((pix >= 0) & (pix < 12 * 64 * 64)))
+    assert bad == (pix == -1).sum() and bad > 0
+    assert np.all(c[pix == -1] == 0)
