@@ -491,7 +491,16 @@ static void orc_apply_ninv(const orc_problem *pb, const double *x, double *y)
 static void orc_apply_A(const orc_problem *pb, const double *x, double *out)
 {
     int64_t ns = pb->ndet * pb->nsamp;
+    double *xs = NULL;
+    if (pb->valid) {
+        /* S^T x: unknowns exist only on valid pixels */
+        xs = (double *)malloc(sizeof(double) * 3 * (size_t)pb->npix);
+        for (int64_t p = 0; p < pb->npix; ++p)
+            for (int k = 0; k < 3; ++k) xs[3 * p + k] = pb->valid[p] ? x[3 * p + k] : 0.0;
+        x = xs;
+    }
     orc_P(ns, pb->pix, pb->cw, pb->sw, x, pb->tod);
+    free(xs);
     orc_apply_ninv(pb, pb->tod, pb->tod2);
     orc_PT(pb->npix, ns, pb->pix, pb->cw, pb->sw, pb->tod2, out, NULL);
     if (pb->valid)

@@ -115,7 +115,9 @@ def test_graph_and_eager_identical(fx, dev, banded):
         xe, _, ie = fx.mapmaker_cg(P, N, dt, maxiter=30, tol=0.0, precision="f64", use_graph=False, check_every=7)
     s.synchronize()
     assert ig.iters == ie.iters == 30
-    assert torch.equal(xg, xe)   # deterministic reductions, same launch sequence
+    # dots are reduced in a fixed order; the scatter's FP64 atomics are not, so the two runs
+    # differ only by that rounding order, amplified over 30 iterations
+    assert (torch.linalg.norm(xg - xe) / torch.linalg.norm(xe)).item() < 1e-9
 
 
 def test_batched_observations_solved_independently(fx, dev, orc):
