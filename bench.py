@@ -43,13 +43,27 @@ def parse():
     ap.add_argument("--no-cg1e8", action="store_true", help="skip the solve-to-1e-8 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the fused P^T N^-1 P apply (profiling runs; not a bench line)")
+    ap.add_argument("--ndet", type=int, default=None, help="override the detector count (profiling runs)")
+    ap.add_argument("--nsamp", type=int, default=None, help="override the samples per detector (profiling runs)")
+    ap.add_argument("--nside", type=int, default=None, help="override nside (profiling runs)")
+    ap.add_argument("--acc", default="f32", choices=["f32", "f32_kahan", "f64"])
+    global ARGS
+    ARGS = ap.parse_args()
+    return ARGS
+
+
+ARGS = None
 
 
 def workload(small: bool):
-    if small:
-        return dict(nside=128, ndet=32, nsamp=1 << 16)
-    return dict(nside=512, ndet=256, nsamp=1 << 20)
+    wl = dict(nside=128, ndet=32, nsamp=1 << 16) if small else dict(nside=512, ndet=256, nsamp=1 << 20)
+    for k in ("nside", "ndet", "nsamp"):
+        v = getattr(ARGS, k, None) if ARGS is not None else None
+        if v:
+            wl[k] = int(v)
+    return wl
 
 
 def dist_setup(args):
@@ -241,9 +255,25 @@ def main():
     stream.synchronize()
     d_h = d.cpu().pin_memory()
 
+    if args.apply_only:
+        xin = torch.randn(npix, 3, dtype=torch.float64, device=dev, generator=g)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fx.ptnp_apply(P, N, xin, None, "f32", args.acc)
+            nat.furax_profile_reset()
+            nat.furax_profile_enable(True)
+            for _ in range(args.steps):
+                fx.ptnp_apply(P, N, xin, None, "f32", args.acc)
+            stream.synchronize()
+            nat.furax_profile_enable(False)
+        ms, n = nat.furax_profile_read(0)
+        print(json.dumps({"apply_only": True, **wl, "acc": args.acc, "ms_per_apply": ms / max(n, 1),
+                          "gsamples_per_s": S / (ms / max(n, 1) / 1e3) / 1e9, "launches": n}), flush=True)
+        return
+
     def step():
         P.refresh()
-        return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=1e-30,
+        return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=0.0,
                               max_outer=1, true_residual=False, check_every=10)
 
     # ---------------- warm-up
@@ -288,7 +318,9 @@ def main():
     # ---------------- roofline of the dominant kernel (fused FP32 P^T N^-1 P apply)
     peak, peak_kind = measured_peaks()
     alg_bytes = 12.0 * S + 2.0 * 24.0 * npix
-    apply_ms = f32_ms / max(f32_n, 1)
+    if f32_n == 0:
+        raise RuntimeError("no fused-apply launch was timed inside the timed region")
+    apply_ms = f32_ms / f32_n
     achieved = alg_bytes / (apply_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "fused_f32_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",

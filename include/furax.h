@@ -191,7 +191,8 @@ typedef struct {
     int32_t precision;     /* FURAX_F64: plain FP64 PCG. FURAX_F32: mixed precision — inner PCG
                               with the FP32 operator, outer defect correction with the FP64 operator */
     int32_t acc;           /* accumulation of the inner operator (FURAX_F32 only) */
-    double inner_tol;      /* FURAX_F32: relative reduction asked of each inner solve (e.g. 1e-5) */
+    double inner_tol;      /* FURAX_F32: relative reduction asked of each inner solve (e.g. 1e-5);
+                              0 runs the inner solve to the iteration cap */
     int32_t max_outer;     /* FURAX_F32: cap on outer corrections */
     int32_t use_graph;     /* capture the iteration in a CUDA graph and replay it */
     int32_t check_every;   /* iterations between host convergence checks (>= 1) */

@@ -553,8 +553,8 @@ furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n
     REQUIRE(o->tol >= 0.0, "tol must be >= 0");
     REQUIRE(valid_dtype(o->precision), "unknown precision %d", o->precision);
     REQUIRE(valid_acc(o->acc), "unknown accumulation mode %d", o->acc);
-    REQUIRE(o->precision == FURAX_F64 || (o->inner_tol > 0.0 && o->inner_tol < 1.0 && o->max_outer >= 1),
-            "mixed precision needs 0 < inner_tol < 1 and max_outer >= 1");
+    REQUIRE(o->precision == FURAX_F64 || (o->inner_tol >= 0.0 && o->inner_tol < 1.0 && o->max_outer >= 1),
+            "mixed precision needs 0 <= inner_tol < 1 and max_outer >= 1");
     REQUIRE(o->check_every >= 1, "check_every must be >= 1");
     REQUIRE(!res->hist || res->hist_len >= 0, "hist_len must be >= 0");
     return mapmaker_cg(p, n, d, d_t, x, valid, o, res, (cudaStream_t)stream);

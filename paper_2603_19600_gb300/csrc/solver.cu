@@ -488,14 +488,14 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
     const furax_pointing *p = b.p;
     furax_status rc;
     int acc = b.acc;
-    if (e0) cudaEventRecord(e0, st);
+    if (e0) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);  // a timing node inside a captured graph
     if (b.precision == FURAX_F64) {
         if ((rc = launch_fused_f64(p, b.n, w->p, w->acc64, st))) return rc;
         acc = FURAX_ACC_F64;
     } else {
         if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st))) return rc;
     }
-    if (e1) cudaEventRecord(e1, st);
+    if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     cg_q_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
     cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc);
     cg_update_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
