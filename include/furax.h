@@ -245,6 +245,11 @@ furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, 
  * Diagnostics.
  * ------------------------------------------------------------------------------------- */
 
+/* Synchronise `stream` and report whether any bounded device-side wait of this handle's kernels
+ * gave up since the last check (FURAX_ETIMEOUT, and the error word is cleared) or not (FURAX_OK).
+ * furax_mapmaker_cg checks this itself at its synchronisation points. */
+furax_status furax_device_status(furax_pointing_t *p, void *stream);
+
 /* Thread-local message describing the last error ("" if none). Never NULL. */
 const char *furax_last_error(void);
 /* Number of kernels this library has launched in this process (graph replays count their

@@ -57,6 +57,7 @@ _SIGS = {
     "furax_pointing_destroy": [_V],
     "furax_pointing_info": [_V, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "furax_pointing_refresh": [_V, _V],
+    "furax_device_status": [_V, _V],
     "furax_pointing_set_psi_offset": [_V, _V, _V],
     "furax_profile_read": [_I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)],
     "furax_pointing_expand": [_V, _V, _V, _V, _I32, _V],
@@ -189,6 +190,11 @@ def furax_pointing_info(h):
 
 def furax_pointing_refresh(h, stream=None) -> None:
     _call("furax_pointing_refresh", h, _stream(stream))
+
+
+def furax_device_status(h, stream=None) -> None:
+    """Raise FuraxError (FURAX_ETIMEOUT) if a bounded device-side wait gave up."""
+    _call("furax_device_status", h, _stream(stream))
 
 
 def furax_profile_enable(on: bool) -> None:

@@ -139,8 +139,11 @@ void build_layout(const furax_obs_desc *desc, Layout &L)
             t.len = (int32_t)std::min<int64_t>(PTILE, o.npix - k * PTILE);
             L.ptiles.push_back(t);
         }
-        for (int32_t j = 0; j < o.ndet; ++j)
-            for (int64_t t0 = 0; t0 < o.nsamp; t0 += TILE) {
+        // Time-major order: the CTAs resident at any moment process every detector over the
+        // same stretch of time, i.e. one compact swath of sky, so the map gathers and the
+        // per-pixel reductions stay in L2 instead of spanning the whole map.
+        for (int64_t t0 = 0; t0 < o.nsamp; t0 += TILE)
+            for (int32_t j = 0; j < o.ndet; ++j) {
                 Tile t;
                 t.t0 = t0; t.obs = i; t.det = j;
                 t.len = (int32_t)std::min<int64_t>(TILE, o.nsamp - t0);
@@ -194,6 +197,22 @@ void furax_profile_reset(void)
     g_prof_cnt[0] = g_prof_cnt[1] = 0;
 }
 
+furax_status furax_device_status(furax_pointing_t *p, void *stream)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    furax_status rc = check_cuda(cudaMemcpyAsync(&h, p->d_err, sizeof h, cudaMemcpyDeviceToHost, st), "read status");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "status sync");
+    if (rc) return rc;
+    if (h) {
+        cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), st);
+        cudaStreamSynchronize(st);
+        return set_error(FURAX_ETIMEOUT, "a bounded device-side wait gave up (error word %u)", h);
+    }
+    return FURAX_OK;
+}
+
 furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream)
 {
     REQUIRE(p, "pointing handle is NULL");
@@ -215,7 +234,7 @@ static void pointing_free(furax_pointing *p)
     cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs);
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
     cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc_lo); cudaFree(p->ws_acc64); cudaFree(p->ws_x64);
-    cudaFree(p->ws_tod); cudaFree(p->ws_tod2); cudaFree(p->ws_hits);
+    cudaFree(p->ws_tod); cudaFree(p->ws_tod2); cudaFree(p->ws_hits); cudaFree(p->d_err);
     delete p;
 }
 
@@ -248,6 +267,13 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
 
     furax_pointing *p = new furax_pointing();
     p->mode = mode;
+    {
+        int dev = 0, sms = 1;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            p->n_sm = std::max(1, sms);
+        cudaGetLastError();
+    }
     p->n_obs = desc->n_obs;
     p->q_bore = desc->q_bore;
     p->q_det = desc->q_det;
@@ -271,7 +297,9 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
     if ((rc = up((void **)&p->d_obs, p->obs.data(), sizeof(ObsInfo) * p->obs.size())) ||
         (rc = up((void **)&p->d_tiles, p->tiles.data(), sizeof(Tile) * p->tiles.size())) ||
         (rc = up((void **)&p->d_ptiles, p->ptiles.data(), sizeof(PTile) * p->ptiles.size())) ||
-        (rc = ensure_ws(p, (void **)&p->d_psi_cs, sizeof(double2) * det))) {
+        (rc = ensure_ws(p, (void **)&p->d_psi_cs, sizeof(double2) * det)) ||
+        (rc = ensure_ws(p, (void **)&p->d_err, sizeof(unsigned))) ||
+        (rc = check_cuda(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), st), "memset"))) {
         pointing_free(p);
         return rc;
     }

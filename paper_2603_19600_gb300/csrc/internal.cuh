@@ -113,6 +113,8 @@ struct furax_pointing {
     double *c64 = nullptr, *s64 = nullptr;
     int64_t nsamp_total = 0, npix_total = 0, ndet_total = 0, nbore_total = 0, n_invalid = 0;
     int32_t max_ndet = 0;
+    int32_t n_sm = 1;                 // SMs of the device (persistent grids)
+    unsigned *d_err = nullptr;        // device error word: bounded waits that gave up
     // workspaces, allocated on first use and freed by destroy
     float4 *ws_map32 = nullptr;       // [npix] padded FP32 copy of a map for the gather
     float4 *ws_acc_hi = nullptr;      // [npix] FP32 accumulator (I,Q,U,-)

@@ -36,6 +36,7 @@ struct CgWs {
     double *partial = nullptr;    // [n_ptiles][KD]
     CgScalars *sc = nullptr;      // [n_obs]
     CgScalars *h_sc = nullptr;    // pinned host mirror
+    unsigned *h_err = nullptr;    // pinned copy of the handle's device error word
     double *hist = nullptr;       // [hist_cap] device
     int32_t hist_cap = 0;
     cudaGraphExec_t graph = nullptr;
@@ -69,6 +70,7 @@ static void free_cg(CgWs *w)
     cudaFree(w->partial); cudaFree(w->sc); cudaFree(w->hist);
     for (cudaEvent_t e : w->ev) cudaEventDestroy(e);
     if (w->h_sc) cudaFreeHost(w->h_sc);
+    if (w->h_err) cudaFreeHost(w->h_err);
     if (w->graph) cudaGraphExecDestroy(w->graph);
     delete w;
 }
@@ -461,7 +463,8 @@ static furax_status get_ws(furax_pointing *p, int hist_cap, CgWs **out)
     if (!rc) rc = alloc((void **)&w->sc, sizeof(CgScalars) * p->n_obs);
     w->hist_cap = std::max(hist_cap, 1);
     if (!rc) rc = alloc((void **)&w->hist, sizeof(double) * w->hist_cap);
-    if (!rc && cudaMallocHost((void **)&w->h_sc, sizeof(CgScalars) * p->n_obs) != cudaSuccess) {
+    if (!rc && (cudaMallocHost((void **)&w->h_sc, sizeof(CgScalars) * p->n_obs) != cudaSuccess ||
+                cudaMallocHost((void **)&w->h_err, sizeof(unsigned)) != cudaSuccess)) {
         cudaGetLastError();
         rc = set_error(FURAX_ENOMEM, "pinned host allocation failed");
     }
@@ -590,7 +593,11 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
         if ((rc = check_cuda(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(CgScalars) * p->n_obs, cudaMemcpyDeviceToHost, st),
                              "read PCG state")))
             return rc;
+        if ((rc = check_cuda(cudaMemcpyAsync(w->h_err, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                             "read device status")))
+            return rc;
         if ((rc = check_cuda(cudaStreamSynchronize(st), "PCG sync"))) return rc;
+        if (*w->h_err) return set_error(FURAX_ETIMEOUT, "a bounded device-side wait gave up during PCG");
         for (int i = 0; i < graph_timed; ++i) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, w->ev[2 * i], w->ev[2 * i + 1]) == cudaSuccess)
@@ -728,7 +735,11 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
         } else {
             res->hist_written = 0;
         }
+        if ((rc = check_cuda(cudaMemcpyAsync(w->h_err, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                             "read device status")))
+            return rc;
         if ((rc = check_cuda(cudaStreamSynchronize(st), "final sync"))) return rc;
+        if (*w->h_err) return set_error(FURAX_ETIMEOUT, "a bounded device-side wait gave up");
         int64_t nv = 0;
         for (int64_t i = 0; i < np; ++i) nv += hv[i];
         res->n_valid = nv;

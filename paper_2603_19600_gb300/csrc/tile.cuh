@@ -34,7 +34,7 @@ __device__ __forceinline__ T white_scale(const NoiseView &nv, int64_t gdet)
     else return nv.p64[gdet];
 }
 
-constexpr size_t kF32Smem = sizeof(float) * (XS + MAXTAPS + 2 * CS) + sizeof(int32_t) * CS;
+constexpr size_t kF32Smem = sizeof(float) * (XS + MAXTAPS + 2 * XS) + sizeof(int32_t) * XS;
 constexpr size_t kF64Smem = sizeof(double) * (XS + MAXTAPS + 2 * CS) + sizeof(int32_t) * CS;
 
 // Kernel shared-memory setup for each translation unit (called once, outside stream capture).
