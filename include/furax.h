@@ -176,6 +176,26 @@ furax_status furax_ptnp_apply(const furax_pointing_t *p, const furax_noise_t *n,
                               double *out, const uint8_t *valid, int32_t precision, int32_t acc,
                               void *stream);
 
+/* The FP32 normal-equations operator of furax_ptnp_apply (precision FURAX_F32, FURAX_ACC_F32) for
+ * callers that cannot allocate device memory: code running inside a memory budget fixed up front
+ * (a pre-sized pool of a host framework, a plugin that must not grow the process's footprint) or
+ * code that must not synchronise the device, as cudaMalloc/cudaFree may. It takes one observation's
+ * expanded pointing directly and allocates nothing; the paper has no counterpart (a deployment
+ * variant). Its scratch (an FP32 copy of x and the FP32 accumulator) is one file-scope device array
+ * sized for nside <= 256 (786,432 pixels, 25 MB), held by every GPU that loads the library until
+ * the process exits.
+ *   pix, c, s: device [ndet][nsamp] int32 / FP32 / FP32 (as furax_pointing_expand gives them; pixel
+ *   -1 or outside the map = skipped); taps: device FP32 [ndet][ntaps], the symmetric band
+ *   c_0..c_{K-1} (ntaps = 1: white noise, taps = 1/sigma^2); valid: device uint8 [12 nside^2] or
+ *   NULL; x, out: device FP64 [12 nside^2][3], must not overlap.
+ * Errors: FURAX_EINVAL for null pointers, bad sizes, or nside > 256. The first call on a device
+ * looks up the scratch address (cudaGetSymbolAddress) with that device current: make it before
+ * any stream capture. Every call shares the scratch and it keeps the last call's contents (the
+ * kernels clear what must start at zero); calls that overlap on the GPU race on it. */
+furax_status furax_ptnp_apply_noalloc(const int32_t *pix, const float *c, const float *s, int32_t ndet,
+                                      int64_t nsamp, int32_t nside, const float *taps, int32_t ntaps,
+                                      const uint8_t *valid, const double *x, double *out, void *stream);
+
 /* b = S P^T N^-1 d in FP64 (d of dtype d_t, device [nsamp_total]; b device FP64 [npix_total][3]). */
 furax_status furax_rhs(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
                        const uint8_t *valid, double *b, void *stream);

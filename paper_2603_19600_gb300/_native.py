@@ -69,6 +69,7 @@ _SIGS = {
     "furax_blockdiag_precond": [_V, _V, _D, _V, _V, _V, _V, _V],
     "furax_ptnp_apply": [_V, _V, _V, _V, _V, _I32, _I32, _V],
     "furax_rhs": [_V, _V, _V, _I32, _V, _V, _V],
+    "furax_ptnp_apply_noalloc": [_V, _V, _V, _I32, _I64, _I32, _V, _I32, _V, _V, _V, _V],
     "furax_mapmaker_cg": [_V, _V, _V, _I32, _V, _V, ctypes.POINTER(CgOpts), ctypes.POINTER(CgResult), _V],
     "furax_chi2_grad": [_V, _V, _V, _I32, _V, _V, _V, _V, _I32, _V],
 }
@@ -260,6 +261,15 @@ def furax_blockdiag_precond(hp, hn, rcond_min, blocks_inv, valid, hits=None, rco
 def furax_ptnp_apply(hp, hn, x, out, valid=None, precision=FURAX_F32, acc=FURAX_ACC_F32, stream=None) -> None:
     _call("furax_ptnp_apply", hp, hn, _ptr(x, torch.float64, None, "x"), _ptr(out, torch.float64, x.numel(), "out"),
           _ptr(valid, torch.uint8, None, "valid"), precision, acc, _stream(stream))
+
+
+def furax_ptnp_apply_noalloc(pix, c, s, ndet, nsamp, nside, taps, x, out, valid=None, stream=None) -> None:
+    """out = S P^T N^-1 P S^T x in FP32 for callers that cannot allocate (see include/furax.h)."""
+    n = int(ndet) * int(nsamp)
+    _call("furax_ptnp_apply_noalloc", _ptr(pix, torch.int32, n, "pix"), _ptr(c, torch.float32, n, "c"),
+          _ptr(s, torch.float32, n, "s"), int(ndet), int(nsamp), int(nside), _ptr(taps, torch.float32, None, "taps"),
+          taps.numel() // int(ndet), _ptr(valid, torch.uint8, None, "valid"), _ptr(x, torch.float64, None, "x"),
+          _ptr(out, torch.float64, x.numel(), "out"), _stream(stream))
 
 
 def furax_rhs(hp, hn, d, b, valid=None, stream=None) -> None:
