@@ -309,6 +309,7 @@ def main():
     nat.furax_profile_enable(False)
     f32_ms, f32_n = nat.furax_profile_read(0)
     f64_ms, f64_n = nat.furax_profile_read(1)
+    df_ms, df_n = nat.furax_profile_read(2)
     ms_local = e0.elapsed_time(e1)
     ms_max = reduce_max(ms_local, world, dev)
     ms_per_step = ms_max / args.steps
@@ -336,6 +337,7 @@ def main():
         "roofline": roofline,
         "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
         "fp64_fused_ms_per_launch": (f64_ms / f64_n) if f64_n else None,
+        "rhs_double_fp32_ms_per_launch": (df_ms / df_n) if df_n else None,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -368,14 +370,18 @@ def main():
     if rank == 0 and not args.no_cg1e8 and world == 1:
         res = {}
         with torch.cuda.stream(stream):
-            P.refresh()
+            # mixed: FP32 inner operator on a hi+lo weight cache, FP64-accurate outer residual;
+            # plain: FP64 operator on an FP64 weight cache. Same system; caches built before timing.
+            PM = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_mixed", stream=stream)
+            NM = fx.Noise.banded(PM, taps)
             stream.synchronize()
             t0 = time.perf_counter()
-            xm, _, im = fx.mapmaker_cg(P, N, d, maxiter=2000, tol=1e-8, precision="f32", acc="f32", inner_tol=1e-5,
+            xm, _, im = fx.mapmaker_cg(PM, NM, d, maxiter=2000, tol=1e-8, precision="f32", acc="f32", inner_tol=1e-5,
                                        max_outer=10)
             stream.synchronize()
             res["mixed"] = {"seconds": time.perf_counter() - t0, "iters": im.iters, "outer": im.outer,
                             "true_rel_res": im.true_rel_res, "converged": im.converged}
+            PM.close()
             P64 = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_f64", stream=stream)
             N64 = fx.Noise.banded(P64, taps)
             stream.synchronize()

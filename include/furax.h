@@ -53,6 +53,11 @@ typedef int32_t furax_status;
 
 typedef enum { FURAX_F32 = 0, FURAX_F64 = 1 } furax_dtype;
 
+/* Arithmetic of an operator application (furax_ptnp_apply): FURAX_F32, FURAX_F64, or
+ * FURAX_PREC_F32X2 = FP64-accurate results computed on FP32 units (double-FP32 "Dot2" band
+ * product with exact FP32 products and two-sums; FP64 gather and per-pixel sums). */
+#define FURAX_PREC_F32X2 2
+
 /* Accumulation of P^T into pixels. */
 typedef enum {
     FURAX_ACC_F64 = 0,       /* FP64 atomic sums per pixel component */
@@ -65,7 +70,10 @@ typedef enum {
 typedef enum {
     FURAX_POINTING_ON_THE_FLY = 0, /* recompute pixel and weights from quaternions each call */
     FURAX_POINTING_CACHE_F32 = 1,  /* cache int32 pixel + FP32 (cos 2psi, sin 2psi): 12 B/sample */
-    FURAX_POINTING_CACHE_F64 = 2   /* cache int32 pixel + FP64 weights: 20 B/sample */
+    FURAX_POINTING_CACHE_F64 = 2,  /* cache int32 pixel + FP64 weights: 20 B/sample */
+    FURAX_POINTING_CACHE_MIXED = 3 /* cache int32 pixel + FP32 weights (hi) + FP32 corrections (lo),
+                                      hi + lo = the FP64 weight to ~2^-48: FP32 operators stream
+                                      12 B/sample, FP64-accurate ones 20 B/sample */
 } furax_pointing_mode;
 
 typedef enum { FURAX_NOISE_WHITE = 0, FURAX_NOISE_BANDED = 1 } furax_noise_kind;
@@ -116,6 +124,13 @@ furax_status furax_pointing_set_psi_offset(furax_pointing_t *p, const double *ps
  * pix: device int32 [nsamp_total]; c, s: device [nsamp_total] of dtype w_t. */
 furax_status furax_pointing_expand(const furax_pointing_t *p, int32_t *pix, void *c, void *s,
                                    int32_t w_t, void *stream);
+
+/* furax_pointing_expand recomputes with the exact FP64 recipe. This copies out what the FP32
+ * operators actually read from an FP32 or mixed cache: pixels (identical to the FP64 recipe's)
+ * and FP32 weights without offsets (FURAX_POINTING_CACHE_F32 fills them from FP32 arithmetic,
+ * relative error a few 1e-7 away from the poles; FURAX_POINTING_CACHE_MIXED rounds the FP64 values).
+ * pix, c, s: device [nsamp_total]. Errors: EINVAL for other modes. */
+furax_status furax_pointing_cache(const furax_pointing_t *p, int32_t *pix, float *c, float *s, void *stream);
 
 /* tod = P map: tod[i] = I_p + Q_p cos 2psi_i + U_p sin 2psi_i (0 for invalid samples).
  * map: device [npix_total][3] of map_t; tod: device [nsamp_total] of tod_t (overwritten).
@@ -281,8 +296,8 @@ const char *furax_version(void);
 /* Kernel timing: when enabled, the library brackets every launch of the fused P^T N^-1 P
  * kernels (FP32 and FP64) with CUDA events on the launching stream (also inside captured
  * graphs) and accumulates their durations, read at the solver's synchronisation points and
- * at furax_profile_read. kernel: 0 = FP32 fused apply, 1 = FP64 fused apply (incl. right-hand
- * side). Writes the total milliseconds and the number of timed launches. */
+ * at furax_profile_read. kernel: 0 = FP32 fused apply, 1 = FP64 fused apply (incl. the FP64
+ * right-hand side), 2 = double-FP32 fused apply (incl. its right-hand side). Writes the total milliseconds and the number of timed launches. */
 void furax_profile_enable(int32_t on);
 furax_status furax_profile_read(int32_t kernel, double *total_ms, int64_t *count);
 void furax_profile_reset(void);

@@ -19,7 +19,8 @@ FURAX_OK = 0
 FURAX_ENOTCONVERGED = 1
 FURAX_F32, FURAX_F64 = 0, 1
 FURAX_ACC_F64, FURAX_ACC_F32_KAHAN, FURAX_ACC_F32 = 0, 1, 2
-FURAX_POINTING_ON_THE_FLY, FURAX_POINTING_CACHE_F32, FURAX_POINTING_CACHE_F64 = 0, 1, 2
+FURAX_POINTING_ON_THE_FLY, FURAX_POINTING_CACHE_F32, FURAX_POINTING_CACHE_F64, FURAX_POINTING_CACHE_MIXED = 0, 1, 2, 3
+FURAX_PREC_F32X2 = 2
 FURAX_NOISE_WHITE, FURAX_NOISE_BANDED = 0, 1
 
 _DT = {torch.float32: FURAX_F32, torch.float64: FURAX_F64}
@@ -57,6 +58,7 @@ _SIGS = {
     "furax_pointing_destroy": [_V],
     "furax_pointing_info": [_V, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "furax_pointing_refresh": [_V, _V],
+    "furax_pointing_cache": [_V, _V, _V, _V, _V],
     "furax_device_status": [_V, _V],
     "furax_pointing_set_psi_offset": [_V, _V, _V],
     "furax_profile_read": [_I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)],
@@ -220,6 +222,11 @@ def furax_pointing_set_psi_offset(h, psi_offset, stream=None) -> None:
 def furax_pointing_expand(h, pix, c, s, stream=None) -> None:
     _call("furax_pointing_expand", h, _ptr(pix, torch.int32, None, "pix"), _ptr(c, None, pix.numel(), "c"),
           _ptr(s, c.dtype, pix.numel(), "s"), _dt(c), _stream(stream))
+
+
+def furax_pointing_cache(h, pix, c, s, stream=None) -> None:
+    _call("furax_pointing_cache", h, _ptr(pix, torch.int32, None, "pix"), _ptr(c, torch.float32, pix.numel(), "c"),
+          _ptr(s, torch.float32, pix.numel(), "s"), _stream(stream))
 
 
 def furax_pointing_apply(h, m, tod, stream=None) -> None:

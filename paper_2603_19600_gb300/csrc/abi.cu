@@ -67,8 +67,8 @@ void destroy_cg_ws(furax_pointing *p);
 // ---- kernel timing
 static std::atomic<bool> g_prof_on{false};
 static std::mutex g_prof_mu;
-static double g_prof_ms[2] = {0.0, 0.0};
-static int64_t g_prof_cnt[2] = {0, 0};
+static double g_prof_ms[3] = {0.0, 0.0, 0.0};
+static int64_t g_prof_cnt[3] = {0, 0, 0};
 struct PendingPair { int kind; cudaEvent_t a, b; };
 static std::vector<PendingPair> g_pending;
 static std::vector<cudaEvent_t> g_pool;
@@ -181,7 +181,7 @@ void furax_profile_enable(int32_t on) { g_prof_on = on != 0; }
 
 furax_status furax_profile_read(int32_t kernel, double *total_ms, int64_t *count)
 {
-    REQUIRE(kernel == 0 || kernel == 1, "kernel must be 0 (FP32 fused) or 1 (FP64 fused)");
+    REQUIRE(kernel >= 0 && kernel <= 2, "kernel must be 0 (FP32 fused), 1 (FP64 fused) or 2 (double-FP32 fused)");
     prof_flush();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (total_ms) *total_ms = g_prof_ms[kernel];
@@ -193,8 +193,8 @@ void furax_profile_reset(void)
 {
     prof_flush();
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof_ms[0] = g_prof_ms[1] = 0.0;
-    g_prof_cnt[0] = g_prof_cnt[1] = 0;
+    g_prof_ms[0] = g_prof_ms[1] = g_prof_ms[2] = 0.0;
+    g_prof_cnt[0] = g_prof_cnt[1] = g_prof_cnt[2] = 0;
 }
 
 furax_status furax_device_status(furax_pointing_t *p, void *stream)
@@ -213,6 +213,20 @@ furax_status furax_device_status(furax_pointing_t *p, void *stream)
     return FURAX_OK;
 }
 
+furax_status furax_pointing_cache(const furax_pointing_t *p, int32_t *pix, float *c, float *s, void *stream)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    REQUIRE(pix && c && s, "pix, c and s must be device pointers");
+    REQUIRE(p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED,
+            "only the FP32 and mixed caches hold FP32 weights");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)p->nsamp_total;
+    furax_status rc = check_cuda(cudaMemcpyAsync(pix, p->pix, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(c, p->c32, sizeof(float) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(s, p->s32, sizeof(float) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    return rc;
+}
+
 furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream)
 {
     REQUIRE(p, "pointing handle is NULL");
@@ -220,9 +234,11 @@ furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream)
     if (p->mode == FURAX_POINTING_ON_THE_FLY) return FURAX_OK;
     const bool had = p->has_psi;
     p->has_psi = false;
-    furax_status rc = p->mode == FURAX_POINTING_CACHE_F32
-                          ? launch_expand(p, p->pix, p->c32, p->s32, nullptr, nullptr, nullptr, st, false)
-                          : launch_expand(p, p->pix, nullptr, nullptr, p->c64, p->s64, nullptr, st, false);
+    furax_status rc;
+    if (p->mode == FURAX_POINTING_CACHE_F32) rc = launch_expand_fast(p, nullptr, st);
+    else if (p->mode == FURAX_POINTING_CACHE_MIXED)
+        rc = launch_expand(p, p->pix, p->c32, p->s32, nullptr, nullptr, nullptr, st, false, p->c32lo, p->s32lo);
+    else rc = launch_expand(p, p->pix, nullptr, nullptr, p->c64, p->s64, nullptr, st, false);
     p->has_psi = had;
     return rc;
 }
@@ -233,6 +249,7 @@ static void pointing_free(furax_pointing *p)
     destroy_cg_ws(p);
     cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs);
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
+    cudaFree(p->c32lo); cudaFree(p->s32lo); cudaFree(p->ws_bore_m);
     cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc_lo); cudaFree(p->ws_acc64); cudaFree(p->ws_x64);
     cudaFree(p->ws_tod); cudaFree(p->ws_tod2); cudaFree(p->ws_hits); cudaFree(p->d_err);
     delete p;
@@ -257,7 +274,8 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
     *out = nullptr;
     furax_status rc = check_desc(desc);
     if (rc) return rc;
-    REQUIRE(mode == FURAX_POINTING_ON_THE_FLY || mode == FURAX_POINTING_CACHE_F32 || mode == FURAX_POINTING_CACHE_F64,
+    REQUIRE(mode == FURAX_POINTING_ON_THE_FLY || mode == FURAX_POINTING_CACHE_F32 || mode == FURAX_POINTING_CACHE_F64 ||
+                mode == FURAX_POINTING_CACHE_MIXED,
             "unknown pointing mode %d", mode);
     REQUIRE(desc->q_bore && desc->q_det, "q_bore and q_det must be device pointers");
     REQUIRE(aligned16(desc->q_bore) && aligned16(desc->q_det), "quaternion arrays must be 16-byte aligned");
@@ -315,16 +333,20 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
     }
     // Expansion: caches pixel + weights, or (on the fly) only validates the quaternions.
     int32_t *pix = nullptr;
-    if (mode == FURAX_POINTING_CACHE_F32) {
+    if (mode == FURAX_POINTING_CACHE_F32 || mode == FURAX_POINTING_CACHE_MIXED) {
+        const bool mixed = mode == FURAX_POINTING_CACHE_MIXED;
         if ((rc = ensure_ws(p, (void **)&p->pix, sizeof(int32_t) * tod)) ||
             (rc = ensure_ws(p, (void **)&p->c32, sizeof(float) * tod)) ||
-            (rc = ensure_ws(p, (void **)&p->s32, sizeof(float) * tod))) {
+            (rc = ensure_ws(p, (void **)&p->s32, sizeof(float) * tod)) ||
+            (mixed && (rc = ensure_ws(p, (void **)&p->c32lo, sizeof(float) * tod))) ||
+            (mixed && (rc = ensure_ws(p, (void **)&p->s32lo, sizeof(float) * tod)))) {
             cudaFree(d_bad); pointing_free(p); return rc;
         }
         pix = p->pix;
         // weights are cached without the offsets; kernels rotate them per detector
         const bool had = p->has_psi; p->has_psi = false;
-        rc = launch_expand(p, p->pix, p->c32, p->s32, nullptr, nullptr, d_bad, st, false);
+        if (mixed) rc = launch_expand(p, p->pix, p->c32, p->s32, nullptr, nullptr, d_bad, st, false, p->c32lo, p->s32lo);
+        else rc = launch_expand_fast(p, d_bad, st);
         p->has_psi = had;
     } else if (mode == FURAX_POINTING_CACHE_F64) {
         if ((rc = ensure_ws(p, (void **)&p->pix, sizeof(int32_t) * tod)) ||
@@ -529,7 +551,7 @@ furax_status furax_ptnp_apply(const furax_pointing_t *p, const furax_noise_t *n,
     if (rc) return rc;
     REQUIRE(x && out, "x and out must be device pointers");
     REQUIRE(x != out, "x and out must not alias");
-    REQUIRE(valid_dtype(precision), "unknown precision %d", precision);
+    REQUIRE(valid_dtype(precision) || precision == FURAX_PREC_F32X2, "unknown precision %d", precision);
     REQUIRE(valid_acc(acc), "unknown accumulation mode %d", acc);
     return ptnp_apply(p, n, x, out, valid, precision, acc, (cudaStream_t)stream);
 }
@@ -548,8 +570,9 @@ furax_status furax_rhs(const furax_pointing_t *p, const furax_noise_t *n, const 
     const bool prof = prof_on();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) { prof_pair(&e0, &e1); if (e0) cudaEventRecord(e0, st); }
-    if ((rc = launch_rhs_f64(p, n, d, d_t, pm->ws_acc64, st))) return rc;
-    if (prof) { if (e1) cudaEventRecord(e1, st); prof_push(1, e0, e1); }
+    // FP64-accurate on FP32 pipes (double-FP32 band product); FP64 arithmetic would be ~5x slower here
+    if ((rc = launch_fused_df(p, n, nullptr, d, d_t, pm->ws_acc64, st))) return rc;
+    if (prof) { if (e1) cudaEventRecord(e1, st); prof_push(2, e0, e1); }
     return launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, pm->ws_acc64, valid, b, st);
 }
 

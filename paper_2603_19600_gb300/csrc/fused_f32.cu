@@ -308,7 +308,7 @@ furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, con
     if (p->n_tiles == 0) return FURAX_OK;
     furax_status rc;
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
-    else if (p->mode == FURAX_POINTING_CACHE_F32)
+    else if (p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED)  // FP32 weights: hi
         rc = n->kind == FURAX_NOISE_BANDED ? dispatch_fused_f32_ws<true>(p, n, x32, acc, hi, lo, a64, st)
                                            : dispatch_fused_f32_ws<false>(p, n, x32, acc, hi, lo, a64, st);
     else rc = dispatch_fused_f32<2>(p, n, x32, acc, hi, lo, a64, st);

@@ -95,6 +95,8 @@ static furax_status dispatch_f64(const furax_pointing *p, const furax_noise *n, 
         return b ? run_f64<0, true, FROM_TOD, DT>(p, n, x, d, a64, st) : run_f64<0, false, FROM_TOD, DT>(p, n, x, d, a64, st);
     if (p->mode == FURAX_POINTING_CACHE_F32)
         return b ? run_f64<1, true, FROM_TOD, DT>(p, n, x, d, a64, st) : run_f64<1, false, FROM_TOD, DT>(p, n, x, d, a64, st);
+    if (p->mode == FURAX_POINTING_CACHE_MIXED)
+        return b ? run_f64<3, true, FROM_TOD, DT>(p, n, x, d, a64, st) : run_f64<3, false, FROM_TOD, DT>(p, n, x, d, a64, st);
     return b ? run_f64<2, true, FROM_TOD, DT>(p, n, x, d, a64, st) : run_f64<2, false, FROM_TOD, DT>(p, n, x, d, a64, st);
 }
 
@@ -138,6 +140,9 @@ furax_status prepare_fused_f64()
     if (!rc) rc = prep_f64_mode_band<1, false>();
     if (!rc) rc = prep_f64_mode_band<2, true>();
     if (!rc) rc = prep_f64_mode_band<2, false>();
+    if (!rc) rc = prep_f64_mode_band<3, true>();
+    if (!rc) rc = prep_f64_mode_band<3, false>();
+    if (!rc) rc = prepare_fused_df();
     return rc;
 }
 

@@ -50,7 +50,8 @@ struct PointingView {
     const double *q_det;
     const double2 *psi_cs;  // per global detector (cos 2 delta, sin 2 delta), or nullptr
     const int32_t *pix;     // cache (modes 1, 2)
-    const float *c32, *s32; // cache mode 1
+    const float *c32, *s32; // cache modes 1 and 3 (weights rounded to FP32)
+    const float *c32lo, *s32lo; // cache mode 3: FP64 weight - FP32 weight
     const double *c64, *s64;// cache mode 2
 };
 
@@ -110,6 +111,7 @@ struct furax_pointing {
     bool has_psi = false;
     int32_t *pix = nullptr;
     float *c32 = nullptr, *s32 = nullptr;
+    float *c32lo = nullptr, *s32lo = nullptr;
     double *c64 = nullptr, *s64 = nullptr;
     int64_t nsamp_total = 0, npix_total = 0, ndet_total = 0, nbore_total = 0, n_invalid = 0;
     int32_t max_ndet = 0;
@@ -124,9 +126,10 @@ struct furax_pointing {
     void *ws_tod = nullptr;           // [nsamp] scratch TOD (FP64 size)
     void *ws_tod2 = nullptr;
     int32_t *ws_hits = nullptr;       // [npix] hit counts when the caller passes none
+    float *ws_bore_m = nullptr;       // [nbore][18] boresight rotation matrices (double-FP32)
     fx::CgWs *cg = nullptr;           // solver workspace (allocated by the first solve)
     fx::PointingView view() const {
-        return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c64, s64};
+        return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c32lo, s32lo, c64, s64};
     }
 };
 
@@ -150,8 +153,11 @@ furax_status ensure_ws(furax_pointing *p, void **ptr, size_t bytes);
 
 // ---- launchers (pointing.cu)
 furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, float *s32, double *c64,
-                           double *s64, unsigned long long *n_invalid, cudaStream_t st, bool all_mode);
+                           double *s64, unsigned long long *n_invalid, cudaStream_t st, bool all_mode,
+                           float *c32lo = nullptr, float *s32lo = nullptr);
 furax_status launch_set_psi(furax_pointing *p, const double *psi, cudaStream_t st);
+// FP32 cache fill with certified FP32 pixels and exact FP64 fallback (pointing_fast.cu)
+furax_status launch_expand_fast(const furax_pointing *p, unsigned long long *n_invalid, cudaStream_t st);
 furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void *tod, int tod_t, cudaStream_t st);
 furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void *map, int map_t, int acc,
                        int32_t *hits, int accumulate, cudaStream_t st);
@@ -181,6 +187,10 @@ furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, con
                               float4 *acc_hi, float4 *acc_lo, double *acc64, cudaStream_t st);
 furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, const double *x, double *acc64,
                               cudaStream_t st);
+// FP64-accurate operator on FP32 units (double-FP32 band product): acc64 += P^T N^-1 P x, or
+// acc64 += P^T N^-1 d when d != nullptr.
+furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, const double *x, const void *d, int d_t,
+                             double *acc64, cudaStream_t st);
 // b = P^T N^-1 d accumulated into acc64 (FP64 stencil)
 furax_status launch_rhs_f64(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *acc64,
                             cudaStream_t st);

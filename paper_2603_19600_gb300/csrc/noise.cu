@@ -186,6 +186,8 @@ furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, con
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_chi2<0>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
     else if (p->mode == FURAX_POINTING_CACHE_F32)
         rc = dispatch_chi2<1>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
+    else if (p->mode == FURAX_POINTING_CACHE_MIXED)
+        rc = dispatch_chi2<3>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
     else rc = dispatch_chi2<2>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
     if (rc) return rc;
     count_launches(1);

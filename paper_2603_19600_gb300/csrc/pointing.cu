@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ ti
                                                      const double *__restrict__ q_bore, const double *__restrict__ q_det,
                                                      const double2 *__restrict__ psi_cs, int32_t *__restrict__ pix_out,
                                                      WT *__restrict__ c_out, WT *__restrict__ s_out,
-                                                     unsigned long long *__restrict__ n_invalid)
+                                                     unsigned long long *__restrict__ n_invalid,
+                                                     float *__restrict__ c_lo, float *__restrict__ s_lo)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
@@ -34,6 +35,10 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ ti
         const int64_t i = ob.tod_off + tl.det * ob.nsamp + t;
         pix_out[i] = r.pix;
         if (c_out) { c_out[i] = (WT)c; s_out[i] = (WT)s; }
+        if (c_lo) {  // FP32 correction words: (double)hi + (double)lo == c to ~2^-48
+            c_lo[i] = (float)(c - (double)(float)c);
+            s_lo[i] = (float)(s - (double)(float)s);
+        }
         bad += (r.pix < 0);
     }
     if (n_invalid) {
@@ -43,16 +48,16 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ ti
 }
 
 furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, float *s32, double *c64, double *s64,
-                           unsigned long long *n_invalid, cudaStream_t st, bool)
+                           unsigned long long *n_invalid, cudaStream_t st, bool, float *c32lo, float *s32lo)
 {
     if (p->n_tiles == 0) return FURAX_OK;
     const double2 *cs = p->has_psi ? p->d_psi_cs : nullptr;
     if (c64 || (!c32 && !c64))
         expand_kernel<double><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
-                                                                    c64, s64, n_invalid);
+                                                                    c64, s64, n_invalid, nullptr, nullptr);
     else
         expand_kernel<float><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
-                                                                   c32, s32, n_invalid);
+                                                                   c32, s32, n_invalid, c32lo, s32lo);
     count_launches(1);
     return check_launch("pointing expansion");
 }
@@ -119,6 +124,7 @@ furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void 
     if (p->n_tiles == 0) return FURAX_OK;
     if (p->mode == FURAX_POINTING_ON_THE_FLY) dispatch_P<0>(p, map, map_t, tod, tod_t, st);
     else if (p->mode == FURAX_POINTING_CACHE_F32) dispatch_P<1>(p, map, map_t, tod, tod_t, st);
+    else if (p->mode == FURAX_POINTING_CACHE_MIXED) dispatch_P<3>(p, map, map_t, tod, tod_t, st);
     else dispatch_P<2>(p, map, map_t, tod, tod_t, st);
     count_launches(1);
     return check_launch("pointing apply");
@@ -223,6 +229,7 @@ furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void
     if (p->n_tiles > 0) {
         if (p->mode == FURAX_POINTING_ON_THE_FLY) dispatch_PT<0>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
         else if (p->mode == FURAX_POINTING_CACHE_F32) dispatch_PT<1>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
+        else if (p->mode == FURAX_POINTING_CACHE_MIXED) dispatch_PT<3>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
         else dispatch_PT<2>(p, tod, tod_t, acc, hi, lo, a64, hits, st);
         count_launches(1);
         if ((rc = check_launch("pointing transpose"))) return rc;
@@ -318,6 +325,8 @@ furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rco
             bj_accum_kernel<0><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
         else if (p->mode == FURAX_POINTING_CACHE_F32)
             bj_accum_kernel<1><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
+        else if (p->mode == FURAX_POINTING_CACHE_MIXED)
+            bj_accum_kernel<3><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
         else
             bj_accum_kernel<2><<<g, 256, 0, st>>>(p->d_tiles, pv, n->diag, blocks_inv, h);
         count_launches(1);

@@ -1,0 +1,234 @@
+// Fast pointing expansion for the FP32 cache (PointingOperator, "Map-making classes": the
+// pointing is expanded from the quaternions; HEALPix RING pixels, "Landscape types").
+//
+// GB300 runs FP64 ~70x slower than FP32, and the exact FP64 recipe of pointing_math.cuh costs
+// ~150 FP64 operations per sample. Here each sample is computed on the FP32 pipes and the
+// exact recipe runs only where the FP32 result could differ from it:
+//   * R(q_bore(t)) is formed once per boresight sample in FP64 and stored as double-FP32
+//     (hi + lo, 18 floats); the detector axes R(q_det) z^, R(q_det) x^ once per tile.
+//     d = R(q_bore) d_det and o = R(q_bore) o_det are then evaluated with exact FP32 products
+//     and two-sums, so the FP32 line of sight and orientation are within ~1 ulp of the exact
+//     values (R(a (x) b) = R(a) R(b) for unit quaternions).
+//   * The RING lookup is done in FP32 (atan2f: at most 3 ulp). Every floor() argument is
+//     accepted only if it lies farther from an integer than a bound on its FP32 error
+//     (derived below); the zone test, facet edges and the neighbourhood of the poles likewise.
+//     An accepted floor equals the floor of the exact value, hence the FP64 recipe's floor.
+//   * Samples that fail any test are queued in shared memory and recomputed with the exact
+//     FP64 recipe by the whole CTA (dense, no divergence). Non-unit or non-finite quaternions
+//     always take the exact path, which gives them pixel -1 where the recipe does.
+// Pixels are therefore identical to the FP64 recipe's; weights are FP32 (relative error a few
+// 1e-7 away from the poles).
+//
+// Error budget (u = 2^-24): |d - d_exact|, |o - o_exact| <= 6u per component (rounding of the
+// double-FP32 result plus |q|^2 within 4u of 1). phi: <= 8.5u/rho + 24u (atan2f) + 8u (2 pi
+// wrap); tt = 2 phi/pi: <= 5.4u/rho + 24.4u. Belt arguments N(1/2 + tt -/+ 3z/4): <= 44 N u;
+// cap arguments tp s, (1 - tp) s with s = N sqrt(3 (1-|z|)): <= 51 N u; cap in-ring argument
+// tt * ir: <= 47 N u + 5.4u/rho. The margins used are about twice these.
+#include "internal.cuh"
+#include "pointing_math.cuh"
+
+namespace fx {
+
+constexpr float kU = 5.9604645e-8f;   // 2^-24
+
+// Bore matrices: M_t = R(q_bore(t)) row-major, hi[9] then lo[9]; hi[0] = NaN marks a
+// boresight quaternion that must take the exact path (not finite, or |q|^2 not within 4u of 1).
+__global__ void bore_matrix_kernel(const double *__restrict__ q_bore, int64_t n, float *__restrict__ m)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const Quat q = load_quat(q_bore, t);
+        const double n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
+        float *o = m + 18 * t;
+        if (!(fabs(n2 - 1.0) <= 4.0 * 5.9604644775390625e-8)) {
+            o[0] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const double xx = q.x * q.x, yy = q.y * q.y, zz = q.z * q.z;
+        const double xy = q.x * q.y, xz = q.x * q.z, yz = q.y * q.z;
+        const double wx = q.w * q.x, wy = q.w * q.y, wz = q.w * q.z;
+        const double r[9] = {1.0 - 2.0 * (yy + zz), 2.0 * (xy - wz), 2.0 * (xz + wy),
+                             2.0 * (xy + wz), 1.0 - 2.0 * (xx + zz), 2.0 * (yz - wx),
+                             2.0 * (xz - wy), 2.0 * (yz + wx), 1.0 - 2.0 * (xx + yy)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float h = (float)r[k];
+            o[k] = h;
+            o[9 + k] = (float)(r[k] - (double)h);
+        }
+    }
+}
+
+// Row . vector in double-FP32 (exact products of the hi parts, two-sums), rounded to FP32.
+__device__ __forceinline__ float dot3_df(const float *mh, const float *ml, const float (&vh)[3], const float (&vl)[3])
+{
+    float s = 0.f, err = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float p = __fmul_rn(mh[j], vh[j]);
+        const float e = __fmaf_rn(mh[j], vh[j], -p);
+        const float t = __fadd_rn(s, p);
+        const float bv = __fsub_rn(t, s);
+        const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+        s = t;
+        err = __fmaf_rn(mh[j], vl[j], __fmaf_rn(ml[j], vh[j], __fadd_rn(err, __fadd_rn(te, e))));
+    }
+    return __fadd_rn(s, err);
+}
+
+__device__ __forceinline__ float frac_dist(float v)
+{
+    const float f = v - floorf(v);
+    return fminf(f, 1.f - f);
+}
+
+// FP32 RING lookup with certified floors; false if any decision is within its error bound.
+__device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, int64_t nside, int32_t &pix)
+{
+    const float rho2 = fmaf(dx, dx, dy * dy);
+    if (!(rho2 >= 0.0025f)) return false;              // within ~3 deg of a pole (or NaN)
+    const float rho = sqrtf(rho2);
+    const float za = fabsf(dz);
+    if (fabsf(za - 0.6666667f) <= 64.f * kU) return false;   // zone decision
+    const float N = (float)nside;
+    float phi = atan2f(dy, dx);
+    if (phi < 0.f) phi += 6.2831855f;
+    const float tt = phi * 0.63661977f;
+    if (za <= 0.6666667f) {
+        const float t1 = N * (0.5f + tt), t2 = N * (dz * 0.75f);
+        const float a1 = t1 - t2, a2 = t1 + t2;
+        const float m = 96.f * N * kU + 16.f * kU;
+        if (frac_dist(a1) <= m || frac_dist(a2) <= m) return false;
+        const int64_t jp = (int64_t)floorf(a1), jm = (int64_t)floorf(a2);
+        const int64_t ir = nside + 1 + jp - jm;
+        const int64_t kshift = 1 - (ir & 1);
+        int64_t ip = (jp + jm - nside + kshift) / 2;
+        const int64_t nl4 = 4 * nside;
+        ip %= nl4;
+        if (ip < 0) ip += nl4;
+        const int64_t p = 2 * nside * (nside - 1) + (ir - 1) * nl4 + ip;
+        if (p < 0 || p >= 12 * nside * nside) return false;
+        pix = (int32_t)p;
+        return true;
+    }
+    const float ft = tt - floorf(tt);
+    if (fminf(ft, 1.f - ft) <= 16.f * kU / rho + 64.f * kU) return false;   // facet edge
+    const float tmp = N * sqrtf(3.f * (rho2 / (1.f + za)));
+    const float b1 = ft * tmp, b2 = (1.f - ft) * tmp;
+    const float mc = 112.f * N * kU + 16.f * kU;
+    if (frac_dist(b1) <= mc || frac_dist(b2) <= mc) return false;
+    const int64_t jp = (int64_t)floorf(b1), jm = (int64_t)floorf(b2);
+    const int64_t ir = jp + jm + 1;
+    const float b3 = tt * (float)ir;
+    if (frac_dist(b3) <= 96.f * N * kU + 16.f * kU / rho + 64.f * kU) return false;
+    int64_t ip = (int64_t)floorf(b3);
+    const int64_t nl = 4 * ir;
+    ip %= nl;
+    if (ip < 0) ip += nl;
+    const int64_t p = dz > 0.f ? 2 * ir * (ir - 1) + ip : 12 * nside * nside - 2 * ir * (ir + 1) + ip;
+    if (p < 0 || p >= 12 * nside * nside) return false;
+    pix = (int32_t)p;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                          const double *__restrict__ q_bore, const double *__restrict__ q_det,
+                                                          const float *__restrict__ bm, int32_t *__restrict__ pix_out,
+                                                          float *__restrict__ c_out, float *__restrict__ s_out,
+                                                          unsigned long long *__restrict__ n_invalid)
+{
+    __shared__ int qn;
+    __shared__ int32_t queue[TILE];
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    const Quat qd = load_quat(q_det, gdet);
+    // detector axes (third and first columns of R(q_det)) in double-FP32
+    float dh[3], dl[3], oh[3], ol[3];
+    bool det_ok;
+    {
+        const double n2 = qd.w * qd.w + qd.x * qd.x + qd.y * qd.y + qd.z * qd.z;
+        det_ok = fabs(n2 - 1.0) <= 4.0 * 5.9604644775390625e-8;
+        const double xx = qd.x * qd.x, yy = qd.y * qd.y, zz = qd.z * qd.z;
+        const double xy = qd.x * qd.y, xz = qd.x * qd.z, yz = qd.y * qd.z;
+        const double wx = qd.w * qd.x, wy = qd.w * qd.y, wz = qd.w * qd.z;
+        const double dv[3] = {2.0 * (xz + wy), 2.0 * (yz - wx), 1.0 - 2.0 * (xx + yy)};
+        const double ov[3] = {1.0 - 2.0 * (yy + zz), 2.0 * (xy + wz), 2.0 * (xz - wy)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dh[k] = (float)dv[k]; dl[k] = (float)(dv[k] - (double)dh[k]);
+            oh[k] = (float)ov[k]; ol[k] = (float)(ov[k] - (double)oh[k]);
+        }
+    }
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    const int64_t row = ob.tod_off + tl.det * ob.nsamp;
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int64_t t = tl.t0 + k;
+        const float *m = bm + 18 * (ob.bore_off + t);
+        float mh[9], ml[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) { mh[j] = m[j]; ml[j] = m[9 + j]; }
+        bool ok = det_ok && !isnan(mh[0]);
+        int32_t p = -1;
+        float c = 1.f, s = 0.f;
+        if (ok) {
+            const float dx = dot3_df(mh + 0, ml + 0, dh, dl), dy = dot3_df(mh + 3, ml + 3, dh, dl),
+                        dz = dot3_df(mh + 6, ml + 6, dh, dl);
+            const float ox = dot3_df(mh + 0, ml + 0, oh, ol), oy = dot3_df(mh + 3, ml + 3, oh, ol),
+                        oz = dot3_df(mh + 6, ml + 6, oh, ol);
+            ok = fast_ring_pixel(dx, dy, dz, ob.nside, p);
+            if (ok) {
+                // psi from local north through east (same convention as the exact recipe)
+                const float rho2 = fmaf(dx, dx, dy * dy);
+                const float a = fmaf(-dz, fmaf(ox, dx, oy * dy), rho2 * oz);
+                const float b = fmaf(oy, dx, -ox * dy);
+                const float n2 = fmaf(a, a, b * b);
+                const float inv = 1.f / n2;
+                c = (a * a - b * b) * inv;
+                s = 2.f * a * b * inv;
+            }
+        }
+        if (ok) {
+            pix_out[row + t] = p;
+            c_out[row + t] = c;
+            s_out[row + t] = s;
+        } else {
+            queue[atomicAdd(&qn, 1)] = k;
+        }
+    }
+    __syncthreads();
+    // exact FP64 recipe for the queued samples, densely
+    const int nq = qn;
+    int bad = 0;
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        const int64_t t = tl.t0 + queue[j];
+        const SampleF64 r = point_f64(load_quat(q_bore, ob.bore_off + t), qd, ob.nside);
+        pix_out[row + t] = r.pix;
+        c_out[row + t] = (float)r.c;
+        s_out[row + t] = (float)r.s;
+        bad += r.pix < 0;
+    }
+    if (n_invalid) {
+        bad = __reduce_add_sync(0xffffffffu, bad);
+        if ((threadIdx.x & 31) == 0 && bad) atomicAdd(n_invalid, (unsigned long long)bad);
+    }
+}
+
+furax_status launch_expand_fast(const furax_pointing *p, unsigned long long *n_invalid, cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    furax_status rc;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_bore_m, sizeof(float) * 18 * std::max<int64_t>(1, p->nbore_total))))
+        return rc;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 152 * 16));
+    bore_matrix_kernel<<<g, 256, 0, st>>>(p->q_bore, p->nbore_total, pm->ws_bore_m);
+    count_launches(1);
+    if ((rc = check_launch("boresight matrices"))) return rc;
+    if (p->n_tiles == 0) return FURAX_OK;
+    expand_fast_kernel<<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, pm->ws_bore_m,
+                                                             p->pix, p->c32, p->s32, n_invalid);
+    count_launches(1);
+    return check_launch("fast pointing expansion");
+}
+
+}  // namespace fx

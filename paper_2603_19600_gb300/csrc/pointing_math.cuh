@@ -183,7 +183,8 @@ __device__ __forceinline__ void rotate_psi(T &c, T &s, double2 cs)
 }
 
 // Per-sample pointing from a PointingView, for each storage mode.
-// MODE 0: on the fly (FP64); 1: FP32 cache; 2: FP64 cache. Returns the pixel local to the
+// MODE 0: on the fly (FP64); 1: FP32 cache; 2: FP64 cache; 3: FP32 hi + lo cache (FP32 readers see
+// hi, FP64 readers hi + lo). Returns the pixel local to the
 // observation (-1 if invalid) and the weights in precision T, offset included.
 template <int MODE, typename T>
 __device__ __forceinline__ int32_t get_sample(const PointingView &pv, const ObsInfo &ob, int32_t det, int64_t t,
@@ -205,6 +206,10 @@ __device__ __forceinline__ int32_t get_sample(const PointingView &pv, const ObsI
         const int64_t i = ob.tod_off + det * ob.nsamp + t;
         pix = pv.pix[i];
         if constexpr (MODE == 1) { c = (T)pv.c32[i]; s = (T)pv.s32[i]; }
+        else if constexpr (MODE == 3) {
+            if constexpr (sizeof(T) == 4) { c = pv.c32[i]; s = pv.s32[i]; }
+            else { c = (double)pv.c32[i] + (double)pv.c32lo[i]; s = (double)pv.s32[i] + (double)pv.s32lo[i]; }
+        }
         else { c = (T)pv.c64[i]; s = (T)pv.s64[i]; }
         if (pv.psi_cs && pix >= 0) rotate_psi<T>(c, s, pv.psi_cs[gdet]);
         return pix;

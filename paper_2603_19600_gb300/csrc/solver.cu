@@ -160,7 +160,7 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     const int64_t np = p->npix_total;
     furax_status rc;
-    if (precision == FURAX_F64) {
+    if (precision == FURAX_F64 || precision == FURAX_PREC_F32X2) {
         if ((rc = ensure_ws(pm, (void **)&pm->ws_acc64, sizeof(double) * 3 * np))) return rc;
         const double *xin = x;
         if (valid) {
@@ -169,7 +169,11 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
             xin = pm->ws_x64;
         }
         if ((rc = check_cuda(cudaMemsetAsync(pm->ws_acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
-        if ((rc = timed(1, st, [&] { return launch_fused_f64(p, n, xin, pm->ws_acc64, st); }))) return rc;
+        if (precision == FURAX_F64) {
+            if ((rc = timed(1, st, [&] { return launch_fused_f64(p, n, xin, pm->ws_acc64, st); }))) return rc;
+        } else {
+            if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, xin, nullptr, 0, pm->ws_acc64, st); }))) return rc;
+        }
         return launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, pm->ws_acc64, valid, out, st);
     }
     if ((rc = ensure_ws(pm, (void **)&pm->ws_map32, sizeof(float4) * np))) return rc;
@@ -623,7 +627,13 @@ static furax_status true_residual(const Body &b, const double *x, double *rtrue,
     const furax_pointing *p = b.p;
     furax_status rc;
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * p->npix_total, st), "memset"))) return rc;
-    if ((rc = timed(1, st, [&] { return launch_fused_f64(p, b.n, x, w->acc64, st); }))) return rc;
+    // The plain FP64 solve checks itself with the FP64 operator; the mixed solve with the
+    // FP64-accurate double-FP32 operator (same system, ~2^-48 arithmetic, FP32 pipes).
+    if (b.precision == FURAX_F64) {
+        if ((rc = timed(1, st, [&] { return launch_fused_f64(p, b.n, x, w->acc64, st); }))) return rc;
+    } else {
+        if ((rc = timed(2, st, [&] { return launch_fused_df(p, b.n, x, nullptr, 0, w->acc64, st); }))) return rc;
+    }
     residual_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->bfull, w->acc64, w->valid, rtrue, w->partial);
     double *norms = w->q;   // scratch [n_obs][2] (q is free here)
     obs_norms_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, norms);
@@ -654,7 +664,11 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     if ((rc = launch_bj(p, n, o->rcond_min, w->minv, w->valid, nullptr, nullptr, st))) return rc;
     // Right-hand side b = S P^T N^-1 d in FP64.
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
-    if ((rc = timed(1, st, [&] { return launch_rhs_f64(p, n, d, d_t, w->acc64, st); }))) return rc;
+    if (o->precision == FURAX_F64) {
+        if ((rc = timed(1, st, [&] { return launch_rhs_f64(p, n, d, d_t, w->acc64, st); }))) return rc;
+    } else {
+        if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, nullptr, d, d_t, w->acc64, st); }))) return rc;
+    }
     if ((rc = launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, w->acc64, w->valid, w->bfull, st))) return rc;
     if (valid_out && (rc = check_cuda(cudaMemcpyAsync(valid_out, w->valid, np, cudaMemcpyDeviceToDevice, st), "copy mask")))
         return rc;

@@ -40,5 +40,6 @@ constexpr size_t kF64Smem = sizeof(double) * (XS + MAXTAPS + 2 * CS) + sizeof(in
 // Kernel shared-memory setup for each translation unit (called once, outside stream capture).
 furax_status prepare_fused_f32();
 furax_status prepare_fused_f64();
+furax_status prepare_fused_df();
 
 }  // namespace fx

@@ -15,9 +15,9 @@ import torch
 from . import _native as nat
 
 _MODES = {"on_the_fly": nat.FURAX_POINTING_ON_THE_FLY, "cache_f32": nat.FURAX_POINTING_CACHE_F32,
-          "cache_f64": nat.FURAX_POINTING_CACHE_F64}
+          "cache_f64": nat.FURAX_POINTING_CACHE_F64, "cache_mixed": nat.FURAX_POINTING_CACHE_MIXED}
 _ACC = {"f64": nat.FURAX_ACC_F64, "f32_kahan": nat.FURAX_ACC_F32_KAHAN, "f32": nat.FURAX_ACC_F32}
-_PREC = {"f32": nat.FURAX_F32, "f64": nat.FURAX_F64}
+_PREC = {"f32": nat.FURAX_F32, "f64": nat.FURAX_F64, "f32x2": nat.FURAX_PREC_F32X2}
 
 
 class Pointing:
@@ -79,6 +79,14 @@ class Pointing:
         c = torch.empty(self.nsamp_total, dtype=dtype, device=self.device)
         s = torch.empty_like(c)
         nat.furax_pointing_expand(self.handle, pix, c, s)
+        return pix, c, s
+
+    def cache(self):
+        """Pixels and FP32 weights as cached for the FP32 operators (FP32 or mixed cache modes)."""
+        pix = torch.empty(self.nsamp_total, dtype=torch.int32, device=self.device)
+        c = torch.empty(self.nsamp_total, dtype=torch.float32, device=self.device)
+        s = torch.empty_like(c)
+        nat.furax_pointing_cache(self.handle, pix, c, s)
         return pix, c, s
 
     def apply(self, m, out=None, dtype=None):

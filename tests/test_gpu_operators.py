@@ -62,7 +62,7 @@ def test_kahan_accumulation_is_compensated(fx, dev, orc):
     nd, ns = 8, 200000
     o = synth.Observation(1, synth.satellite_scan(ns), synth.hex_focal_plane(nd))
     P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
-    pix, c, s = P.expand(torch.float32)
+    pix, c, s = P.cache()
     g = np.random.default_rng(5)
     y = (g.integers(-2 ** 20, 2 ** 20, nd * ns) * 2.0 ** -10 + 1000.0).astype(np.float32)
     yt = torch.as_tensor(y, device=dev)
@@ -142,7 +142,7 @@ def test_blockdiag_copointed_closed_form(fx, dev):
     h = bj["hits"].cpu().numpy()
     v = bj["valid"].cpu().numpy()
     assert np.array_equal(v, h >= 4)
-    assert np.allclose(bj["rcond"].cpu().numpy()[v], 0.5, rtol=1e-6)
+    assert np.allclose(bj["rcond"].cpu().numpy()[v], 0.5, rtol=1e-5)
 
 
 @pytest.mark.parametrize("noise", ["banded", "white"])
@@ -174,9 +174,39 @@ def test_rhs_matches_oracle(fx, dev, orc, prob):
     N = fx.Noise.banded(P, taps)
     d = synth.one_over_f_noise(16, 20000, synth.rng(7, 3)).astype(np.float32)
     bj = orc.bj(o.npix, opix, oc, os_, orc.Noise(taps=taps))
-    # FP32 weights in the cache: compare with the oracle on the same rounded weights
-    c32 = oc.astype(np.float32).astype(np.float64)
-    s32 = os_.astype(np.float32).astype(np.float64)
+    # FP32 weights in the cache: compare with the oracle on the same weights
+    _, cc, sc = P.cache()
+    c32 = cc.cpu().numpy().astype(np.float64).reshape(oc.shape)
+    s32 = sc.cpu().numpy().astype(np.float64).reshape(oc.shape)
     ref = orc.rhs(o.npix, opix, c32, s32, orc.Noise(taps=taps), bj["valid"], d.astype(np.float64))
     got = fx.rhs(P, N, torch.as_tensor(d.ravel(), device=dev), torch.as_tensor(bj["valid"].astype(np.uint8), device=dev))
     assert rel(got.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("noise", ["banded", "white"])
+@pytest.mark.parametrize("mode", ["cache_mixed", "cache_f64", "on_the_fly"])
+def test_double_fp32_operator_is_fp64_accurate(fx, dev, orc, prob, noise, mode):
+    """The double-FP32 band product (FP32 pipes) matches the FP64 oracle to FP64-like accuracy
+    when the weights are FP64-accurate (mixed hi+lo cache, FP64 cache, on the fly)."""
+    o, opix, oc, os_, taps, sigma2 = prob
+    P = fx.Pointing.from_observations([o], mode=mode, device=dev)
+    N = fx.Noise.banded(P, taps) if noise == "banded" else fx.Noise.white(P, sigma2)
+    on = orc.Noise(taps=taps) if noise == "banded" else orc.Noise(sigma2=sigma2)
+    valid = orc.bj(o.npix, opix, oc, os_, on)["valid"]
+    x = synth.gaussian_sky(o.nside, synth.rng(7, 4))
+    ref = orc.apply_ata(o.npix, opix, oc, os_, on, valid, x)
+    got = fx.ptnp_apply(P, N, torch.as_tensor(x, device=dev), torch.as_tensor(valid.astype(np.uint8), device=dev),
+                        precision="f32x2").cpu().numpy()
+    assert rel(got, ref) < 1e-12
+
+
+def test_mixed_cache_holds_fp64_weights(fx, dev, orc, prob):
+    o, opix, oc, os_, *_ = prob
+    P = fx.Pointing.from_observations([o], mode="cache_mixed", device=dev)
+    pix, c, s = P.expand(torch.float64)
+    assert np.array_equal(pix.cpu().numpy().reshape(opix.shape), opix)
+    # the FP32 operator of this mode reads the rounded weights, the FP64-accurate ones hi + lo
+    m = synth.gaussian_sky(o.nside, synth.rng(7, 5))
+    ref = orc.P(opix, oc, os_, m).ravel()
+    assert rel(P.apply(torch.as_tensor(m, device=dev), dtype=torch.float64).cpu().numpy(), ref) < 1e-14
+    assert rel(P.apply(torch.as_tensor(m, device=dev).float()).cpu().numpy(), ref) < 1e-6

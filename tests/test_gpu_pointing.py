@@ -50,6 +50,31 @@ def test_expand_matches_oracle(fx, dev, orc, case):
         P.close()
 
 
+def _rho2(orc, qb, qd):
+    ns, nd = qb.shape[0], qd.shape[0]
+    d, _ = orc.quat_axes(orc.quat_mul(np.tile(qb, (nd, 1)), np.repeat(qd, ns, axis=0)))
+    return (d[:, 0] ** 2 + d[:, 1] ** 2).reshape(nd, ns)
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_fp32_cache_matches_oracle(fx, dev, orc, case):
+    """The FP32 cache is filled on the FP32 pipes with certified floors and an exact FP64
+    fallback: pixels identical to the recipe's, weights within a few 1e-7 (relative error
+    ~5 u / rho, with samples closer than rho = 0.05 to a pole recomputed exactly)."""
+    name, nside, ndet, nsamp, fp, offsets = case
+    o = _obs(nside, ndet, nsamp, fp, False)
+    opix, oc, os_, bad = orc.pointing(nside, o.q_bore, o.q_det)
+    P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    pix, c, s = P.cache()
+    assert np.array_equal(pix.cpu().numpy().reshape(opix.shape), opix)
+    c = c.cpu().numpy().reshape(oc.shape).astype(np.float64)
+    s = s.cpu().numpy().reshape(oc.shape).astype(np.float64)
+    rho = np.sqrt(np.maximum(_rho2(orc, o.q_bore, o.q_det), 1e-300))
+    tol = np.minimum(64 * 2.0 ** -24 / rho, 1e-4) + 2 * 2.0 ** -24
+    assert np.all(np.abs(c - oc) <= tol) and np.all(np.abs(s - os_) <= tol)
+    P.close()
+
+
 def test_batched_ragged_expand(fx, dev, orc):
     obs = [_obs(4, 3, 5000, "hex", False), _obs(64, 7, 4096, "hex", False, t0=500.0),
            _obs(16, 1, 1, "hex", False, t0=900.0), _obs(256, 12, 9001, "hex", True, t0=1000.0)]
@@ -101,6 +126,10 @@ def test_full_c2_pointing_sampled(fx, dev, orc):
         assert np.array_equal(pix[idx].cpu().numpy(), opix[0])
         assert np.array_equal(c[idx].cpu().numpy(), oc[0])
         assert np.array_equal(s[idx].cpu().numpy(), os_[0])
+    # the FP32 cache (certified FP32 floors + exact fallback) holds the recipe's pixel for
+    # every one of the 268 M samples
+    cpix, _, _ = P.cache()
+    assert torch.equal(cpix, pix)
     # hits over the full run: every sample lands on a pixel
     _, hits = P.transpose(torch.ones(P.nsamp_total, dtype=torch.float32, device=dev), acc="f32", hits=True)
     assert int(hits.sum()) == nd * ns

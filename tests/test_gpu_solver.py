@@ -86,9 +86,17 @@ def test_banded_pcg_converges_fp64_and_mixed(fx, dev, orc, banded):
         assert i32.converged, (acc, i32)
         assert i32.true_rel_res <= 1e-8
         assert i32.outer >= 1
-        # the FP32 cache holds rounded weights: the mixed solve converges to the same FP64 system
-        # only up to that rounding, so compare against the solution at the solver's tolerance
+        # the FP32 cache holds rounded weights: this solve converges for the operator with those
+        # weights, which differs from the FP64 one by the rounding (~1e-7)
         assert rel(x32.cpu().numpy()[v], ox[v]) < 1e-5, acc
+    # the mixed cache keeps hi + lo weights: inner FP32 operator, outer FP64-accurate operator,
+    # so the mixed solve reaches the FP64 system's solution at the FP64 solve's tolerance
+    PM = fx.Pointing.from_observations([o], mode="cache_mixed", device=dev)
+    xm, _, im = fx.mapmaker_cg(PM, fx.Noise.banded(PM, taps), dt, maxiter=2000, tol=1e-8, precision="f32",
+                               acc="f32", inner_tol=1e-5)
+    assert im.converged and im.true_rel_res <= 1e-8
+    assert rel(xm.cpu().numpy()[v], ox[v]) < 1e-6
+    assert rel(xm.cpu().numpy()[v], x64.cpu().numpy()[v]) < 1e-6
     assert rel(x64.cpu().numpy()[v], ox[v]) < 1e-6
 
 
