@@ -335,9 +335,11 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
     int32_t *pix = nullptr;
     if (mode == FURAX_POINTING_CACHE_F32 || mode == FURAX_POINTING_CACHE_MIXED) {
         const bool mixed = mode == FURAX_POINTING_CACHE_MIXED;
-        if ((rc = ensure_ws(p, (void **)&p->pix, sizeof(int32_t) * tod)) ||
-            (rc = ensure_ws(p, (void **)&p->c32, sizeof(float) * tod)) ||
-            (rc = ensure_ws(p, (void **)&p->s32, sizeof(float) * tod)) ||
+        // padded to a 16-byte multiple: the operator bulk-copies rows on 16-byte boundaries
+        const int64_t tod4 = (tod + 3) & ~int64_t(3);
+        if ((rc = ensure_ws(p, (void **)&p->pix, sizeof(int32_t) * tod4)) ||
+            (rc = ensure_ws(p, (void **)&p->c32, sizeof(float) * tod4)) ||
+            (rc = ensure_ws(p, (void **)&p->s32, sizeof(float) * tod4)) ||
             (mixed && (rc = ensure_ws(p, (void **)&p->c32lo, sizeof(float) * tod))) ||
             (mixed && (rc = ensure_ws(p, (void **)&p->s32lo, sizeof(float) * tod)))) {
             cudaFree(d_bad); pointing_free(p); return rc;

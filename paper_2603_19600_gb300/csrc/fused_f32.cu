@@ -10,7 +10,6 @@
 // The time-ordered data never leaves the SM. The same skeleton gives the standalone N^-1,
 // the right-hand side P^T N^-1 d and chi^2 with its gradients.
 #include "tile.cuh"
-#include "mbarrier.cuh"
 
 namespace fx {
 
@@ -129,154 +128,6 @@ __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict
     }
 }
 
-// ------------------------------------------------------------------------------------
-// Persistent, warp-specialised version for the cached FP32 pointing (the hot path).
-// One CTA per SM walks the time-major tile list with stride gridDim.x. Warps 0-7 (producers)
-// stream a tile's cached pointing and gather its map values into one of two shared-memory
-// stages; warps 8-15 (consumers) run the band product and the scatter on the other stage.
-// The stages are handed over with mbarriers (full: 256 producer arrivals, empty: 256
-// consumer arrivals), so memory latency, FMA work and L2 reductions of consecutive tiles
-// overlap instead of alternating.
-// ------------------------------------------------------------------------------------
-constexpr int kWsThreads = 2 * FT;
-constexpr int kWsStages = 2;
-
-struct WsStage {
-    float xs[XS];
-    float c[XS];
-    float s[XS];
-    int32_t pix[XS];
-    float taps[MAXTAPS];
-};
-
-constexpr size_t kWsSmem = sizeof(WsStage) * kWsStages + 2 * kWsStages * sizeof(uint64_t);
-
-template <int ACC, bool BANDED>
-__global__ void __launch_bounds__(kWsThreads, 1)
-    fused_f32_ws_kernel(const Tile *__restrict__ tiles, int64_t n_tiles, PointingView pv, NoiseView nv,
-                        const float4 *__restrict__ x32, float4 *__restrict__ acc_hi, float4 *__restrict__ acc_lo,
-                        double *__restrict__ acc64, unsigned *__restrict__ err)
-{
-    extern __shared__ __align__(16) unsigned char wsm[];
-    WsStage *stage = reinterpret_cast<WsStage *>(wsm);
-    uint64_t *full = reinterpret_cast<uint64_t *>(wsm + sizeof(WsStage) * kWsStages);
-    uint64_t *empty = full + kWsStages;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kWsStages; ++s) { mbar_init(&full[s], FT); mbar_init(&empty[s], FT); }
-    }
-    __syncthreads();
-
-    const bool producer = threadIdx.x < FT;
-    const int tid = threadIdx.x - (producer ? 0 : FT);
-    constexpr int halo = BANDED ? kHalo : 0;
-    int64_t it = 0;
-    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
-        const int sidx = (int)(it % kWsStages);
-        const uint32_t parity = (uint32_t)((it / kWsStages) & 1);
-        WsStage &S = stage[sidx];
-        const Tile tl = tiles[ti];
-        const ObsInfo ob = pv.obs[tl.obs];
-        const int64_t gdet = ob.det_off + tl.det;
-        const int nload = tl.len + 2 * halo;
-
-        if (producer) {
-            if (!mbar_wait(&empty[sidx], parity ^ 1u, err)) break;
-            if (BANDED && tid < MAXTAPS) S.taps[tid] = tid < nv.ntaps ? nv.p32[gdet * nv.ntaps + tid] : 0.f;
-            const int64_t row = ob.tod_off + tl.det * ob.nsamp;
-            const int64_t t_first = tl.t0 - halo;
-            int32_t pk[kPerThread];
-            float ck[kPerThread], sk[kPerThread];
-#pragma unroll
-            for (int k = 0; k < kPerThread; ++k) {
-                const int u = tid + k * FT;
-                const int64_t t = t_first + u;
-                pk[k] = -1; ck[k] = 0.f; sk[k] = 0.f;
-                if (u < nload && t >= 0 && t < ob.nsamp) {
-                    pk[k] = __ldcs(pv.pix + row + t);
-                    ck[k] = __ldcs(pv.c32 + row + t);
-                    sk[k] = __ldcs(pv.s32 + row + t);
-                }
-            }
-            if (pv.psi_cs) {
-                const double2 cs = pv.psi_cs[gdet];
-#pragma unroll
-                for (int k = 0; k < kPerThread; ++k) rotate_psi<float>(ck[k], sk[k], cs);
-            }
-#pragma unroll
-            for (int k = 0; k < kPerThread; ++k) {
-                const int u = tid + k * FT;
-                if (u < nload) {
-                    float v = 0.f;
-                    if (pk[k] >= 0) {
-                        const float4 m = __ldg(x32 + ob.map_off + pk[k]);
-                        v = fmaf(m.z, sk[k], fmaf(m.y, ck[k], m.x));
-                    }
-                    S.xs[spos(u)] = v;
-                    S.pix[spos(u)] = pk[k];
-                    S.c[spos(u)] = ck[k];
-                    S.s[spos(u)] = sk[k];
-                }
-            }
-            mbar_arrive(&full[sidx]);
-        } else {
-            if (!mbar_wait(&full[sidx], parity, err)) break;
-            const int base = tid * FR;
-            if (base < tl.len) {
-                float y[FR];
-                if constexpr (BANDED) {
-                    band_product<float, FR>(S.xs, S.taps, base, y);
-                } else {
-                    const float w = white_scale<float>(nv, gdet);
-#pragma unroll
-                    for (int r = 0; r < FR; ++r) y[r] = S.xs[spos(base + r)] * w;
-                }
-                int32_t pr[FR];
-                float cr[FR], sr[FR];
-#pragma unroll
-                for (int r = 0; r < FR; ++r) {
-                    const int u = base + r + halo;
-                    pr[r] = base + r < tl.len ? S.pix[spos(u)] : -1;
-                    cr[r] = S.c[spos(u)];
-                    sr[r] = S.s[spos(u)];
-                }
-                mbar_arrive(&empty[sidx]);   // the stage is no longer read: release it early
-#pragma unroll
-                for (int r = 0; r < FR; ++r) {
-                    if (pr[r] < 0) continue;
-                    const int64_t gp = ob.map_off + pr[r];
-                    const float4 v = make_float4(y[r], y[r] * cr[r], y[r] * sr[r], 0.f);
-                    if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
-                    else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
-                    else {
-                        red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
-                        red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
-                        red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
-                    }
-                }
-            } else {
-                mbar_arrive(&empty[sidx]);
-            }
-        }
-    }
-}
-
-template <bool BANDED>
-static furax_status dispatch_fused_f32_ws(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
-                                          float4 *hi, float4 *lo, double *a64, cudaStream_t st)
-{
-    const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
-    const PointingView pv = p->view();
-    const NoiseView nv = n->view();
-    if (acc == FURAX_ACC_F32)
-        return launch_dyn(fused_f32_ws_kernel<FURAX_ACC_F32, BANDED>, g, kWsThreads, kWsSmem, st, p->d_tiles,
-                          p->n_tiles, pv, nv, x32, hi, lo, a64, p->d_err);
-    if (acc == FURAX_ACC_F32_KAHAN)
-        return launch_dyn(fused_f32_ws_kernel<FURAX_ACC_F32_KAHAN, BANDED>, g, kWsThreads, kWsSmem, st, p->d_tiles,
-                          p->n_tiles, pv, nv, x32, hi, lo, a64, p->d_err);
-    return launch_dyn(fused_f32_ws_kernel<FURAX_ACC_F64, BANDED>, g, kWsThreads, kWsSmem, st, p->d_tiles, p->n_tiles,
-                      pv, nv, x32, hi, lo, a64, p->d_err);
-}
-
 template <int MODE, bool BANDED>
 static furax_status dispatch_fused_f32_acc(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
                                            float4 *hi, float4 *lo, double *a64, cudaStream_t st)
@@ -309,8 +160,7 @@ furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, con
     furax_status rc;
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
     else if (p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED)  // FP32 weights: hi
-        rc = n->kind == FURAX_NOISE_BANDED ? dispatch_fused_f32_ws<true>(p, n, x32, acc, hi, lo, a64, st)
-                                           : dispatch_fused_f32_ws<false>(p, n, x32, acc, hi, lo, a64, st);
+        rc = launch_fused_tma(p, n, x32, acc, hi, lo, a64, st);
     else rc = dispatch_fused_f32<2>(p, n, x32, acc, hi, lo, a64, st);
     if (rc) return rc;
     count_launches(1);
@@ -329,13 +179,7 @@ static furax_status prep_f32_mode_band()
 
 furax_status prepare_fused_f32()
 {
-    furax_status rc = FURAX_OK;
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F32, true>, kWsSmem);
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F32_KAHAN, true>, kWsSmem);
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F64, true>, kWsSmem);
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F32, false>, kWsSmem);
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F32_KAHAN, false>, kWsSmem);
-    if (!rc) rc = allow_smem((const void *)fused_f32_ws_kernel<FURAX_ACC_F64, false>, kWsSmem);
+    furax_status rc = prepare_fused_tma();
     if (!rc) rc = prep_f32_mode_band<0, true>();
     if (!rc) rc = prep_f32_mode_band<0, false>();
     if (!rc) rc = prep_f32_mode_band<1, true>();

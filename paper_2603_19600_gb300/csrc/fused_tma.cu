@@ -1,0 +1,289 @@
+// Persistent, TMA-pipelined FP32 operator acc += P^T N^-1 P x32 for the cached FP32
+// pointing (the hot path of the map-making PCG: the estimator A = (H.T @ N.I @ H).I @ H.T @ N.I
+// of the Furax paper's Software Design listing, with the per-detector block decomposition of
+// "Algebraic reductions").
+//
+// One CTA per SM walks the tile list (one detector x up to TILE samples per tile) with stride
+// gridDim.x. Three warp roles hand tiles to each other through shared-memory rings guarded by
+// mbarriers:
+//   loader (1 warp, 1 thread): bulk-copies (cp.async.bulk, completion counted in bytes on an
+//     mbarrier) the cached pixel index and FP32 weights of the tile and its 63-sample halos
+//     into one of kRawStages stages, up to kRawStages - 1 tiles ahead of the consumers;
+//   gather (7 warps): reads a landed stage, gathers the map values of the tile's pixels from
+//     the FP32 map in L2 (all loads of a thread issued before any is used) and writes the
+//     projected samples P x into one of kXsStages stages;
+//   consumer (8 warps): applies N^-1 (the 127-term symmetric band, 16 consecutive outputs per
+//     thread from a sliding register window) and scatters y (1, cos 2psi, sin 2psi) with one
+//     16-byte L2 reduction per sample, lane-consecutive in time so that neighbouring samples
+//     of a warp share cache lines.
+// The pointing stream is read from HBM exactly once (plus 126 halo samples per tile); the map
+// and the accumulators stay in L2. Every wait is bounded: a wait that gives up sets the error
+// word and the role leaves its loop; the loader waits (bounded) for its own copies in flight
+// before it exits.
+#include "tile.cuh"
+#include "mbarrier.cuh"
+
+namespace fx {
+
+constexpr int kTmaGather = 7;                      // gather warps
+constexpr int kTmaConsumer = 8;                    // consumer warps
+constexpr int kTmaThreads = 32 * (kTmaGather + kTmaConsumer + 1);
+constexpr int kRawStages = 3;
+constexpr int kXsStages = 2;
+// Elements of one pointing stream copied per tile: tile + halos, widened to 16-byte boundaries.
+constexpr int kRawN = 4232;
+static_assert(kRawN % 4 == 0 && kRawN >= TILE + 2 * kHalo + 6, "raw stage must hold an aligned tile + halos");
+constexpr int kGatherPer = (TILE + 2 * kHalo + 32 * kTmaGather - 1) / (32 * kTmaGather);
+constexpr int kYs = spos(TILE) + 1;
+
+struct TmaSmem {
+    int32_t pix[kRawStages][kRawN];
+    float c[kRawStages][kRawN];
+    float s[kRawStages][kRawN];
+    float xs[kXsStages][XS];
+    float taps[kXsStages][MAXTAPS];
+    float ys[kYs];
+    uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
+};
+constexpr size_t kTmaSmem = sizeof(TmaSmem);
+static_assert(kTmaSmem <= 227 * 1024, "shared memory per CTA");
+static_assert(sizeof(int32_t) * kRawN % 16 == 0, "stage arrays stay 16-byte aligned");
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; completion is signalled on `bar` as transferred bytes.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// AND of `ok` over the 256 consumer threads (named barrier 1); every consumer thread must call it.
+__device__ __forceinline__ bool consumers_all(bool ok)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)ok), "n"(32 * kTmaConsumer)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kTmaConsumer) : "memory");
+}
+
+// Tile geometry in the flat cache: the copied range [g0, g0 + n) covers every in-stream sample
+// of the tile and its halos; sample t of the detector sits at stage index row + t - g0.
+struct TileSpan {
+    int64_t row, g0;
+    int32_t n;
+};
+
+__device__ __forceinline__ TileSpan tile_span(const Tile &tl, const ObsInfo &ob, int halo)
+{
+    TileSpan sp;
+    sp.row = ob.tod_off + (int64_t)tl.det * ob.nsamp;
+    const int64_t t_lo = tl.t0 - halo > 0 ? tl.t0 - halo : 0;
+    const int64_t t_hi = tl.t0 + tl.len + halo < ob.nsamp ? tl.t0 + tl.len + halo : ob.nsamp;
+    sp.g0 = (sp.row + t_lo) & ~int64_t(3);
+    const int64_t g1 = (sp.row + t_hi + 3) & ~int64_t(3);
+    sp.n = (int32_t)(g1 - sp.g0);
+    return sp;
+}
+
+template <int ACC, bool BANDED>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    fused_tma_kernel(const Tile *__restrict__ tiles, int64_t n_tiles, PointingView pv, NoiseView nv,
+                     const float4 *__restrict__ x32, float4 *__restrict__ acc_hi, float4 *__restrict__ acc_lo,
+                     double *__restrict__ acc64, unsigned *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char tsm[];
+    TmaSmem &S = *reinterpret_cast<TmaSmem *>(tsm);
+    constexpr int halo = BANDED ? kHalo : 0;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRawStages; ++i) { mbar_init(&S.raw_full[i], 1); mbar_init(&S.raw_empty[i], 32 * kTmaConsumer); }
+        for (int i = 0; i < kXsStages; ++i) { mbar_init(&S.xs_full[i], 32 * kTmaGather); mbar_init(&S.xs_empty[i], 32 * kTmaConsumer); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kTmaGather + kTmaConsumer) {
+        // ---------------- loader
+        if ((threadIdx.x & 31) != 0) return;
+        int64_t it = 0;
+        for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
+            const int r = (int)(it % kRawStages);
+            const uint32_t par = (uint32_t)((it / kRawStages) & 1);
+            if (!mbar_wait(&S.raw_empty[r], par ^ 1u, err)) break;
+            const Tile tl = tiles[ti];
+            const ObsInfo ob = pv.obs[tl.obs];
+            const TileSpan sp = tile_span(tl, ob, halo);
+            const uint32_t bytes = (uint32_t)sp.n * 4u;
+            mbar_expect_tx(&S.raw_full[r], 3u * bytes);
+            bulk_g2s(S.pix[r], pv.pix + sp.g0, bytes, &S.raw_full[r]);
+            bulk_g2s(S.c[r], pv.c32 + sp.g0, bytes, &S.raw_full[r]);
+            bulk_g2s(S.s[r], pv.s32 + sp.g0, bytes, &S.raw_full[r]);
+        }
+        // Copies into a stage complete its current phase; wait for the last one issued into each
+        // stage so that no copy is still writing when the CTA exits.
+        for (int64_t j = it - 1; j >= 0 && j >= it - kRawStages; --j)
+            mbar_wait(&S.raw_full[j % kRawStages], (uint32_t)((j / kRawStages) & 1), err);
+        return;
+    }
+
+    if (warp < kTmaGather) {
+        // ---------------- gather: xs = P x over the tile and its halos
+        const int tid = threadIdx.x;
+        int64_t it = 0;
+        for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
+            const int r = (int)(it % kRawStages);
+            const int q = (int)(it % kXsStages);
+            if (!mbar_wait(&S.xs_empty[q], (uint32_t)(((it / kXsStages) & 1) ^ 1), err)) break;
+            if (!mbar_wait(&S.raw_full[r], (uint32_t)((it / kRawStages) & 1), err)) break;
+            const Tile tl = tiles[ti];
+            const ObsInfo ob = pv.obs[tl.obs];
+            const int64_t gdet = ob.det_off + tl.det;
+            const TileSpan sp = tile_span(tl, ob, halo);
+            if (BANDED && tid < MAXTAPS) S.taps[q][tid] = tid < nv.ntaps ? nv.p32[gdet * nv.ntaps + tid] : 0.f;
+            const int nload = tl.len + 2 * halo;
+            const int64_t t_first = tl.t0 - halo;
+            const int64_t shift = sp.row + t_first - sp.g0;   // stage index of u is u + shift
+            const int32_t *spix = S.pix[r];
+            float4 m[kGatherPer];
+#pragma unroll
+            for (int k = 0; k < kGatherPer; ++k) {
+                const int u = tid + k * 32 * kTmaGather;
+                const int64_t t = t_first + u;
+                const int32_t pix = (u < nload && t >= 0 && t < ob.nsamp) ? spix[u + shift] : -1;
+                m[k] = pix >= 0 ? __ldg(x32 + ob.map_off + pix) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            double2 cs = make_double2(1.0, 0.0);
+            if (pv.psi_cs) cs = pv.psi_cs[gdet];
+#pragma unroll
+            for (int k = 0; k < kGatherPer; ++k) {
+                const int u = tid + k * 32 * kTmaGather;
+                const int64_t t = t_first + u;
+                if (u < nload) {
+                    float v = 0.f;
+                    if (t >= 0 && t < ob.nsamp && spix[u + shift] >= 0) {
+                        float c = S.c[r][u + shift], s = S.s[r][u + shift];
+                        if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+                        v = fmaf(m[k].z, s, fmaf(m[k].y, c, m[k].x));
+                    }
+                    S.xs[q][spos(u)] = v;
+                }
+            }
+            mbar_arrive(&S.xs_full[q]);
+        }
+        return;
+    }
+
+    // ---------------- consumer: y = N^-1 xs, then acc[pix] += y (1, c, s)
+    const int tid = threadIdx.x - 32 * kTmaGather;
+    int64_t it = 0;
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
+        const int r = (int)(it % kRawStages);
+        const int q = (int)(it % kXsStages);
+        const bool ok = mbar_wait(&S.xs_full[q], (uint32_t)((it / kXsStages) & 1), err);
+        const Tile tl = tiles[ti];
+        const ObsInfo ob = pv.obs[tl.obs];
+        const int64_t gdet = ob.det_off + tl.det;
+        const int base = tid * FR;
+        float y[FR];
+        if (ok) {
+            if (base < tl.len) {
+                if constexpr (BANDED) {
+                    band_product<float, FR>(S.xs[q], S.taps[q], base, y);
+                } else {
+                    const float w = white_scale<float>(nv, gdet);
+#pragma unroll
+                    for (int i = 0; i < FR; ++i) y[i] = S.xs[q][spos(base + i)] * w;
+                }
+            }
+            mbar_arrive(&S.xs_empty[q]);
+        }
+        // also orders the previous tile's reads of ys before the writes below
+        if (!consumers_all(ok)) break;
+#pragma unroll
+        for (int i = 0; i < FR; ++i)
+            if (base + i < tl.len) S.ys[spos(base + i)] = y[i];
+        consumers_sync();
+        const TileSpan sp = tile_span(tl, ob, halo);
+        const int64_t shift = sp.row + tl.t0 - sp.g0;   // stage index of core sample u
+        double2 cs = make_double2(1.0, 0.0);
+        if (pv.psi_cs) cs = pv.psi_cs[gdet];
+#pragma unroll 4
+        for (int k = 0; k < FR; ++k) {
+            const int u = tid + k * 32 * kTmaConsumer;
+            if (u >= tl.len) break;
+            const int32_t pix = S.pix[r][u + shift];
+            if (pix < 0) continue;
+            float c = S.c[r][u + shift], s = S.s[r][u + shift];
+            if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+            const float yv = S.ys[spos(u)];
+            const int64_t gp = ob.map_off + pix;
+            const float4 v = make_float4(yv, yv * c, yv * s, 0.f);
+            if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
+            else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
+            else {
+                red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
+                red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
+                red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
+            }
+        }
+        mbar_arrive(&S.raw_empty[r]);
+    }
+}
+
+template <int ACC, bool BANDED>
+static furax_status run_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, float4 *hi, float4 *lo,
+                            double *a64, cudaStream_t st)
+{
+    const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
+    return launch_dyn(fused_tma_kernel<ACC, BANDED>, g, kTmaThreads, kTmaSmem, st, p->d_tiles, p->n_tiles, p->view(),
+                      n->view(), x32, hi, lo, a64, p->d_err);
+}
+
+template <bool BANDED>
+static furax_status dispatch_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
+                                 float4 *lo, double *a64, cudaStream_t st)
+{
+    if (acc == FURAX_ACC_F32) return run_tma<FURAX_ACC_F32, BANDED>(p, n, x32, hi, lo, a64, st);
+    if (acc == FURAX_ACC_F32_KAHAN) return run_tma<FURAX_ACC_F32_KAHAN, BANDED>(p, n, x32, hi, lo, a64, st);
+    return run_tma<FURAX_ACC_F64, BANDED>(p, n, x32, hi, lo, a64, st);
+}
+
+furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
+                              float4 *lo, double *a64, cudaStream_t st)
+{
+    return n->kind == FURAX_NOISE_BANDED ? dispatch_tma<true>(p, n, x32, acc, hi, lo, a64, st)
+                                         : dispatch_tma<false>(p, n, x32, acc, hi, lo, a64, st);
+}
+
+furax_status prepare_fused_tma()
+{
+    furax_status rc = FURAX_OK;
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, true>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, true>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, true>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, false>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, false>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, false>, kTmaSmem);
+    return rc;
+}
+
+}  // namespace fx

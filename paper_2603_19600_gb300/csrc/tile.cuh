@@ -41,5 +41,11 @@ constexpr size_t kF64Smem = sizeof(double) * (XS + MAXTAPS + 2 * CS) + sizeof(in
 furax_status prepare_fused_f32();
 furax_status prepare_fused_f64();
 furax_status prepare_fused_df();
+furax_status prepare_fused_tma();
+
+// Cached FP32 pointing: persistent TMA-pipelined operator (cache rows must be readable up to the
+// next 16-byte boundary past the last sample).
+furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
+                              float4 *lo, double *a64, cudaStream_t st);
 
 }  // namespace fx
