@@ -13,9 +13,11 @@
 //     the FP32 map in L2 (all loads of a thread issued before any is used) and writes the
 //     projected samples P x into one of kXsStages stages;
 //   consumer (8 warps): applies N^-1 (the 127-term symmetric band, 16 consecutive outputs per
-//     thread from a sliding register window) and scatters y (1, cos 2psi, sin 2psi) with one
-//     16-byte L2 reduction per sample, lane-consecutive in time so that neighbouring samples
-//     of a warp share cache lines.
+//     thread from a sliding register window), writes y over the consumed stage and scatters
+//     y (1, cos 2psi, sin 2psi) with one 16-byte L2 reduction per sample, lane-consecutive in
+//     time so that neighbouring samples of a warp share cache lines.
+// Shared memory is kept near 138 KB: the rest of the SM's L1/shared array is L1, where the
+// gathers' misses in flight are staged.
 // The pointing stream is read from HBM exactly once (plus 126 halo samples per tile); the map
 // and the accumulators stay in L2. Every wait is bounded: a wait that gives up sets the error
 // word and the role leaves its loop; the loader waits (bounded) for its own copies in flight
@@ -28,13 +30,12 @@ namespace fx {
 constexpr int kTmaGather = 7;                      // gather warps
 constexpr int kTmaConsumer = 8;                    // consumer warps
 constexpr int kTmaThreads = 32 * (kTmaGather + kTmaConsumer + 1);
-constexpr int kRawStages = 3;
+constexpr int kRawStages = 2;
 constexpr int kXsStages = 2;
 // Elements of one pointing stream copied per tile: tile + halos, widened to 16-byte boundaries.
 constexpr int kRawN = 4232;
 static_assert(kRawN % 4 == 0 && kRawN >= TILE + 2 * kHalo + 6, "raw stage must hold an aligned tile + halos");
 constexpr int kGatherPer = (TILE + 2 * kHalo + 32 * kTmaGather - 1) / (32 * kTmaGather);
-constexpr int kYs = spos(TILE) + 1;
 
 struct TmaSmem {
     int32_t pix[kRawStages][kRawN];
@@ -42,11 +43,13 @@ struct TmaSmem {
     float s[kRawStages][kRawN];
     float xs[kXsStages][XS];
     float taps[kXsStages][MAXTAPS];
-    float ys[kYs];
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
-static_assert(kTmaSmem <= 227 * 1024, "shared memory per CTA");
+// The SM's L1 cache and shared memory share one array, and global-load misses in flight are
+// staged in L1: the map gathers need at most ~150 KB of shared memory per SM to keep their
+// full rate (measured: a 206 KB reservation halves it).
+static_assert(kTmaSmem <= 150 * 1024, "leave L1 room for the gathers in flight");
 static_assert(sizeof(int32_t) * kRawN % 16 == 0, "stage arrays stay 16-byte aligned");
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -204,23 +207,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const int64_t gdet = ob.det_off + tl.det;
         const int base = tid * FR;
         float y[FR];
-        if (ok) {
-            if (base < tl.len) {
-                if constexpr (BANDED) {
-                    band_product<float, FR>(S.xs[q], S.taps[q], base, y);
-                } else {
-                    const float w = white_scale<float>(nv, gdet);
+        if (ok && base < tl.len) {
+            if constexpr (BANDED) {
+                band_product<float, FR>(S.xs[q], S.taps[q], base, y);
+            } else {
+                const float w = white_scale<float>(nv, gdet);
 #pragma unroll
-                    for (int i = 0; i < FR; ++i) y[i] = S.xs[q][spos(base + i)] * w;
-                }
+                for (int i = 0; i < FR; ++i) y[i] = S.xs[q][spos(base + i)] * w;
             }
-            mbar_arrive(&S.xs_empty[q]);
         }
-        // also orders the previous tile's reads of ys before the writes below
+        // Every consumer has read its stencil inputs: y overwrites the stage in place (core
+        // sample u at slot spos(u)), which is released to the gathers after the scatter.
         if (!consumers_all(ok)) break;
+        float *ys = S.xs[q];
 #pragma unroll
         for (int i = 0; i < FR; ++i)
-            if (base + i < tl.len) S.ys[spos(base + i)] = y[i];
+            if (base + i < tl.len) ys[spos(base + i)] = y[i];
         consumers_sync();
         const TileSpan sp = tile_span(tl, ob, halo);
         const int64_t shift = sp.row + tl.t0 - sp.g0;   // stage index of core sample u
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             if (pix < 0) continue;
             float c = S.c[r][u + shift], s = S.s[r][u + shift];
             if (pv.psi_cs) rotate_psi<float>(c, s, cs);
-            const float yv = S.ys[spos(u)];
+            const float yv = ys[spos(u)];
             const int64_t gp = ob.map_off + pix;
             const float4 v = make_float4(yv, yv * c, yv * s, 0.f);
             if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
             }
         }
+        mbar_arrive(&S.xs_empty[q]);
         mbar_arrive(&S.raw_empty[r]);
     }
 }
