@@ -26,30 +26,33 @@ __device__ __forceinline__ void dot2_step(float ch, float cl, float xh, float xl
 }
 
 // y_t = sum_j c_|j-63| x_{t+j-63} for R consecutive outputs, in double-FP32 (S + E).
+// Taps are walked in rolled blocks of 8, each unrolled over 8 taps x R outputs from register
+// windows of R + 7 inputs (a fully unrolled 127 x R body overflows the instruction cache).
 template <int R>
 __device__ __forceinline__ void band_product_df(const float *__restrict__ xh, const float *__restrict__ xl,
                                                 const float *__restrict__ th, const float *__restrict__ tl, int base,
                                                 float (&S)[R], float (&E)[R])
 {
-    float wh[R], wl[R];
+    constexpr int JB = 8;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        wh[r] = xh[spos(base + r)];
-        wl[r] = xl[spos(base + r)];
-        S[r] = 0.f;
-        E[r] = 0.f;
-    }
+    for (int r = 0; r < R; ++r) { S[r] = 0.f; E[r] = 0.f; }
+#pragma unroll 1
+    for (int j0 = 0; j0 < kBand; j0 += JB) {
+        float wh[R + JB - 1], wl[R + JB - 1];
 #pragma unroll
-    for (int j = 0; j < kBand; ++j) {
-        const int k = j < kHalo ? kHalo - j : j - kHalo;
-        const float ch = th[k], cl = tl[k];
+        for (int i = 0; i < R + JB - 1; ++i) {
+            wh[i] = xh[spos(base + j0 + i)];
+            wl[i] = xl[spos(base + j0 + i)];
+        }
 #pragma unroll
-        for (int r = 0; r < R; ++r) dot2_step(ch, cl, wh[r], wl[r], S[r], E[r]);
-        if (j < kBand - 1) {
+        for (int jj = 0; jj < JB; ++jj) {
+            const int j = j0 + jj;
+            if (j < kBand) {
+                const int k = j < kHalo ? kHalo - j : j - kHalo;
+                const float ch = th[k], cl = tl[k];
 #pragma unroll
-            for (int r = 0; r < R - 1; ++r) { wh[r] = wh[r + 1]; wl[r] = wl[r + 1]; }
-            wh[R - 1] = xh[spos(base + R + j)];
-            wl[R - 1] = xl[spos(base + R + j)];
+                for (int r = 0; r < R; ++r) dot2_step(ch, cl, wh[r + jj], wl[r + jj], S[r], E[r]);
+            }
         }
     }
 }
@@ -64,7 +67,7 @@ constexpr size_t kDfSmem = sizeof(float) * (2 * XS + 2 * MAXTAPS) + sizeof(float
 
 // acc64 += P^T N^-1 P x  (x: FP64 [npix][3], zero on masked pixels), or acc64 += P^T N^-1 d (FROM_TOD).
 template <int MODE, bool BANDED, bool FROM_TOD, typename DT>
-__global__ void __launch_bounds__(FT, 1) fused_df_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+__global__ void __launch_bounds__(FT, 2) fused_df_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
                                                          const double *__restrict__ x, const DT *__restrict__ d,
                                                          double *__restrict__ acc64)
 {
@@ -143,6 +146,218 @@ __global__ void __launch_bounds__(FT, 1) fused_df_kernel(const Tile *__restrict_
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Right-hand side from FP32 time-ordered data: acc64 + lo += P^T N^-1 d.
+// The input word is exact in FP32, so the compensated band product carries no input low word.
+// The output y = S + E is renormalised to (y_hi, y_lo); each weighted term y w (w = 1, cos, sin)
+// is formed as an exact FP32 product head plus a tail. Heads are accumulated in FP64 (their
+// binary64 value is built from the binary32 encoding, so no FP64 arithmetic is issued); tails,
+// which are ~2^-24 of the heads, are accumulated in FP32 and folded in afterwards.
+// ------------------------------------------------------------------------------------
+
+// Compensated step with an exact FP32 input (no input low word).
+__device__ __forceinline__ void dot2_step_x(float ch, float cl, float x, float &S, float &E)
+{
+    const float p = __fmul_rn(ch, x);
+    const float e = __fmaf_rn(ch, x, -p);
+    const float s = __fadd_rn(S, p);
+    const float bv = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    S = s;
+    E = __fmaf_rn(cl, x, __fadd_rn(E, __fadd_rn(err, e)));
+}
+
+// The taps are walked in blocks of JB (a rolled loop), each block unrolled over JB taps x R
+// outputs from a register window of R + JB - 1 inputs: a fully unrolled 127 x R body does not fit
+// the instruction cache (measured: warps then mostly wait for instructions). The last block is
+// partial (127 = 15 x 8 + 7); its extra window slots read initialised tile slots and are unused.
+constexpr int kDfJB = 8;
+
+template <int R>
+__device__ __forceinline__ void band_product_dfx(const float *__restrict__ xs, const float *__restrict__ th,
+                                                 const float *__restrict__ tl, int base, float (&S)[R], float (&E)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) { S[r] = 0.f; E[r] = 0.f; }
+#pragma unroll 1
+    for (int j0 = 0; j0 < kBand; j0 += kDfJB) {
+        float w[R + kDfJB - 1];
+#pragma unroll
+        for (int i = 0; i < R + kDfJB - 1; ++i) w[i] = xs[spos(base + j0 + i)];
+#pragma unroll
+        for (int jj = 0; jj < kDfJB; ++jj) {
+            const int j = j0 + jj;
+            if (j < kBand) {
+                const int k = j < kHalo ? kHalo - j : j - kHalo;
+                const float ch = th[k], cl = tl[k];
+#pragma unroll
+                for (int r = 0; r < R; ++r) dot2_step_x(ch, cl, w[r + jj], S[r], E[r]);
+            }
+        }
+    }
+}
+
+// binary32 -> binary64 from the IEEE 754 encodings: sign kept, exponent rebiased by
+// 1023 - 127 = 896, significand shifted into the top of the 52-bit field. Exact for normal
+// numbers and zeros; subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63));
+        return (double)f;
+    }
+    const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// Pixel and weights of one sample as double-FP32 pairs (offset rotation included).
+template <int MODE>
+__device__ __forceinline__ int32_t sample_df(const PointingView &pv, const ObsInfo &ob, int32_t det, int64_t t,
+                                             float &ch, float &cl, float &sh, float &sl)
+{
+    if constexpr (MODE == 1 || MODE == 3) {
+        if (!pv.psi_cs) {   // cached FP32 weights (plus the cached low words in mode 3): no FP64
+            const int64_t i = ob.tod_off + det * ob.nsamp + t;
+            const int32_t pix = pv.pix[i];
+            ch = pv.c32[i]; sh = pv.s32[i];
+            if constexpr (MODE == 3) { cl = pv.c32lo[i]; sl = pv.s32lo[i]; }
+            else { cl = 0.f; sl = 0.f; }
+            return pix;
+        }
+    }
+    double c = 0.0, s = 0.0;
+    const int32_t pix = get_sample<MODE, double>(pv, ob, det, t, c, s);
+    split_df(c, ch, cl);
+    split_df(s, sh, sl);
+    return pix;
+}
+
+constexpr size_t kDfRhsSmem = sizeof(float) * (XS + CS + 2 * MAXTAPS);
+
+template <int MODE, bool BANDED>
+__global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+                                                       const float *__restrict__ d, double *__restrict__ acc64,
+                                                       float4 *__restrict__ acc_lo)
+{
+    extern __shared__ __align__(16) float rsm[];
+    float *xs = rsm;            // [XS] d over the tile and its halos; then y_hi of the core samples
+    float *yl = xs + XS;        // [CS] y_lo of the core samples
+    float *th = yl + CS;        // [MAXTAPS]
+    float *tl = th + MAXTAPS;   // [MAXTAPS]
+
+    const Tile tile = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tile.obs];
+    const int64_t gdet = ob.det_off + tile.det;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if (threadIdx.x < MAXTAPS) {
+        double c = 0.0;
+        if constexpr (BANDED) c = threadIdx.x < nv.ntaps ? nv.p64[gdet * nv.ntaps + threadIdx.x] : 0.0;
+        else c = threadIdx.x == 0 ? nv.p64[gdet] : 0.0;
+        split_df(c, th[threadIdx.x], tl[threadIdx.x]);
+    }
+    const int nload = tile.len + 2 * halo;
+    const int64_t row = ob.tod_off + tile.det * ob.nsamp;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tile.t0 - halo + u;
+        xs[spos(u)] = (t >= 0 && t < ob.nsamp) ? d[row + t] : 0.f;
+    }
+    __syncthreads();
+
+    const int base = threadIdx.x * FR;
+    float S[FR], E[FR];
+    if (base < tile.len) {
+        if constexpr (BANDED) {
+            band_product_dfx<FR>(xs, th, tl, base, S, E);
+        } else {
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                S[r] = 0.f;
+                E[r] = 0.f;
+                dot2_step_x(th[0], tl[0], xs[spos(base + r)], S[r], E[r]);
+            }
+        }
+    }
+    __syncthreads();   // every stencil input has been read: y overwrites the tile in place
+    if (base < tile.len) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            if (base + r < tile.len) {
+                const float h = __fadd_rn(S[r], E[r]);          // |S| >= |E|: fast two-sum
+                xs[spos(base + r)] = h;
+                yl[spos(base + r)] = __fsub_rn(E[r], __fsub_rn(h, S[r]));
+            }
+        }
+    }
+    __syncthreads();
+
+    for (int k = threadIdx.x; k < tile.len; k += FT) {
+        float ch, cl, sh, sl;
+        const int32_t pix = sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl);
+        if (pix < 0) continue;
+        const float yh = xs[spos(k)], ylo = yl[spos(k)];
+        const float qc = __fmul_rn(yh, ch), qs = __fmul_rn(yh, sh);
+        const float ec = __fmaf_rn(yh, ch, -qc), es = __fmaf_rn(yh, sh, -qs);
+        const float lc = __fadd_rn(ec, __fmaf_rn(ylo, ch, __fmul_rn(yh, cl)));
+        const float ls = __fadd_rn(es, __fmaf_rn(ylo, sh, __fmul_rn(yh, sl)));
+        const int64_t gp = ob.map_off + pix;
+        red_add_f64(acc64 + 3 * gp + 0, f32_to_f64_bits(yh));
+        red_add_f64(acc64 + 3 * gp + 1, f32_to_f64_bits(qc));
+        red_add_f64(acc64 + 3 * gp + 2, f32_to_f64_bits(qs));
+        red_add_v4(acc_lo + gp, make_float4(ylo, lc, ls, 0.f));
+    }
+}
+
+// acc64 += lo (per pixel, then lo is no longer needed).
+__global__ void fold_lo_kernel(const float4 *__restrict__ lo, double *__restrict__ acc64, int64_t np)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 l = lo[i];
+        acc64[3 * i + 0] += (double)l.x;
+        acc64[3 * i + 1] += (double)l.y;
+        acc64[3 * i + 2] += (double)l.z;
+    }
+}
+
+template <int MODE, bool B>
+static furax_status run_df_rhs(const furax_pointing *p, const furax_noise *n, const float *d, double *a64, float4 *lo,
+                               cudaStream_t st)
+{
+    return launch_dyn(df_rhs_kernel<MODE, B>, (unsigned)p->n_tiles, FT, kDfRhsSmem, st, p->d_tiles, p->view(), n->view(),
+                      d, a64, lo);
+}
+
+static furax_status launch_df_rhs_f32(const furax_pointing *p, const furax_noise *n, const float *d, double *a64,
+                                      cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    furax_status rc;
+    const int64_t np = p->npix_total;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_df_lo, sizeof(float4) * np))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(pm->ws_df_lo, 0, sizeof(float4) * np, st), "memset"))) return rc;
+    const bool b = n->kind == FURAX_NOISE_BANDED;
+    switch (p->mode) {
+    case FURAX_POINTING_ON_THE_FLY:
+        rc = b ? run_df_rhs<0, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<0, false>(p, n, d, a64, pm->ws_df_lo, st);
+        break;
+    case FURAX_POINTING_CACHE_F32:
+        rc = b ? run_df_rhs<1, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<1, false>(p, n, d, a64, pm->ws_df_lo, st);
+        break;
+    case FURAX_POINTING_CACHE_MIXED:
+        rc = b ? run_df_rhs<3, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<3, false>(p, n, d, a64, pm->ws_df_lo, st);
+        break;
+    default:
+        rc = b ? run_df_rhs<2, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<2, false>(p, n, d, a64, pm->ws_df_lo, st);
+    }
+    if (rc) return rc;
+    if ((rc = check_launch("double-FP32 P^T N^-1 d"))) return rc;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, (int64_t)p->n_sm * 8));
+    fold_lo_kernel<<<g, 256, 0, st>>>(pm->ws_df_lo, a64, np);
+    count_launches(2);
+    return check_launch("fold low words");
+}
+
 template <int MODE, bool BANDED, bool FROM_TOD, typename DT>
 static furax_status run_df(const furax_pointing *p, const furax_noise *n, const double *x, const DT *d, double *a64,
                            cudaStream_t st)
@@ -173,6 +388,7 @@ furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, cons
 {
     if (p->n_tiles == 0) return FURAX_OK;
     furax_status rc;
+    if (d && d_t == FURAX_F32) return launch_df_rhs_f32(p, n, (const float *)d, acc64, st);
     if (!d) rc = dispatch_df<false, double>(p, n, x, (const double *)nullptr, acc64, st);
     else if (d_t == FURAX_F64) rc = dispatch_df<true, double>(p, n, nullptr, (const double *)d, acc64, st);
     else rc = dispatch_df<true, float>(p, n, nullptr, (const float *)d, acc64, st);
@@ -188,6 +404,7 @@ static furax_status prep_df_mode_band()
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, false, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, float>, kDfSmem);
+    if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B>, kDfRhsSmem);
     return rc;
 }
 

@@ -122,6 +122,7 @@ struct furax_pointing {
     float4 *ws_acc_hi = nullptr;      // [npix] FP32 accumulator (I,Q,U,-)
     float4 *ws_acc_lo = nullptr;      // [npix] FP32 compensation (KAHAN)
     double *ws_acc64 = nullptr;       // [npix][3] FP64 accumulator
+    float4 *ws_df_lo = nullptr;       // [npix] FP32 low-word accumulator of the double-FP32 RHS
     double *ws_x64 = nullptr;         // [npix][3] masked FP64 copy
     void *ws_tod = nullptr;           // [nsamp] scratch TOD (FP64 size)
     void *ws_tod2 = nullptr;
