@@ -88,6 +88,12 @@ def reduce_max(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def job_value(samples_per_step: float, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput in G units/s: every rank runs the same workload (weak scaling), and the
+    job lasts as long as its slowest rank."""
+    return world * samples_per_step * steps / (ms_max / 1e3) / 1e9
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -202,6 +208,49 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def cg_to_1e8(fx, dev, stream, small=False):
+    """Wall time to a true residual ||b - A64 x||/||b|| <= 1e-8: mixed precision (FP32 inner
+    operator on a hi+lo cache, double-FP32 outer residual) vs plain FP64 PCG, same system."""
+    import torch
+    nside, nd, ns = (128, 32, 1 << 16) if small else (256, 128, 1 << 18)
+    qb = torch.from_numpy(synth.satellite_scan(ns)).to(dev)
+    qd = torch.from_numpy(synth.hex_focal_plane(nd)).to(dev)
+    taps = np.tile(synth.inverse_noise_taps(), (nd, 1))
+    res = {"workload": f"{nd} detectors x {ns} samples, nside {nside}, 64-tap banded N^-1, rcond >= 1e-2"}
+    with torch.cuda.stream(stream):
+        PM = fx.Pointing(qb, qd, [nd], [ns], [nside], mode="cache_mixed", stream=stream)
+        NM = fx.Noise.banded(PM, taps)
+        sky = torch.from_numpy(synth.gaussian_sky(nside, synth.rng(2, 0))).to(dev)
+        d = PM.apply(sky.float())
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 202)
+        f = torch.fft.rfftfreq(ns, d=1.0 / synth.FSAMP_HZ, device=dev, dtype=torch.float64)
+        amp = torch.sqrt(torch.from_numpy(synth.one_over_f_psd(f.cpu().numpy())).to(dev))
+        amp[0] = 0.0
+        w = torch.randn(nd, ns, generator=g, device=dev, dtype=torch.float32)
+        d += torch.fft.irfft(torch.fft.rfft(w, dim=1) * amp.float(), n=ns, dim=1).reshape(-1)
+        P64 = fx.Pointing(qb, qd, [nd], [ns], [nside], mode="cache_f64", stream=stream)
+        N64 = fx.Noise.banded(P64, taps)
+        for name, P, N, prec in (("mixed", PM, NM, "f32"), ("fp64", P64, N64, "f64")):
+            for rep in range(2):   # first run builds the CUDA graph and workspaces
+                stream.synchronize()
+                t0 = time.perf_counter()
+                x, valid, inf = fx.mapmaker_cg(P, N, d, maxiter=5000, tol=1e-8, precision=prec, acc="f32_kahan",
+                                               inner_tol=1e-6, max_outer=20, rcond_min=1e-2)
+                stream.synchronize()
+                sec = time.perf_counter() - t0
+            res[name] = {"seconds": sec, "iters": inf.iters, "outer": inf.outer, "true_rel_res": inf.true_rel_res,
+                         "converged": inf.converged}
+            res[name + "_map"] = x
+        v = valid
+        res["map_rel_diff"] = float(torch.linalg.norm(res.pop("mixed_map")[v] - res["fp64_map"][v])
+                                    / torch.linalg.norm(res["fp64_map"][v]))
+        res.pop("fp64_map")
+        res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+        PM.close()
+        P64.close()
+    return res
+
+
 def _wl_name(wl):
     return (f"satellite scan, {wl['ndet']} detectors (hex focal plane, radius 5 deg) x {wl['nsamp']} samples, "
             f"HEALPix nside {wl['nside']}, 1/f + white noise, 64-tap banded N^-1, {CG_ITERS} PCG iterations")
@@ -314,7 +363,7 @@ def main():
     ms_max = reduce_max(ms_local, world, dev)
     ms_per_step = ms_max / args.steps
     samples_per_step = S * CG_ITERS
-    value = world * samples_per_step * args.steps / (ms_max / 1e3) / 1e9
+    value = job_value(samples_per_step, args.steps, ms_max, world)
 
     # ---------------- roofline of the dominant kernel (fused FP32 P^T N^-1 P apply)
     peak, peak_kind = measured_peaks()
@@ -324,7 +373,7 @@ def main():
     apply_ms = f32_ms / f32_n
     achieved = alg_bytes / (apply_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused_f32_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",
+                "traffic": None, "kernel": "fused_tma_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": apply_ms, "timed_launches": f32_n,
                 "peak_source": f"{peak_kind} hbm_gbs"}
 
@@ -363,39 +412,16 @@ def main():
         stream.synchronize()
         barrier(world)
         e2e_ms = reduce_max(e2.elapsed_time(e3), world, dev)
-        out["e2e"] = {"value": world * samples_per_step * args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+        out["e2e"] = {"value": job_value(samples_per_step, args.steps, e2e_ms, world), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
 
     # ---------------- solve to a true residual of 1e-8: mixed precision vs plain FP64
+    # On the full workload block-Jacobi PCG needs thousands of iterations to reach 1e-8 (the
+    # 1/f-weighted system converges in plateaus), minutes for the FP64 arm; the comparison is
+    # made on a reduced version of the same scan (128 detectors x 2^18 samples, nside 256),
+    # with pixels solved for when rcond >= 1e-2.
     if rank == 0 and not args.no_cg1e8 and world == 1:
-        res = {}
-        with torch.cuda.stream(stream):
-            # mixed: FP32 inner operator on a hi+lo weight cache, FP64-accurate outer residual;
-            # plain: FP64 operator on an FP64 weight cache. Same system; caches built before timing.
-            PM = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_mixed", stream=stream)
-            NM = fx.Noise.banded(PM, taps)
-            stream.synchronize()
-            t0 = time.perf_counter()
-            xm, _, im = fx.mapmaker_cg(PM, NM, d, maxiter=2000, tol=1e-8, precision="f32", acc="f32", inner_tol=1e-5,
-                                       max_outer=10)
-            stream.synchronize()
-            res["mixed"] = {"seconds": time.perf_counter() - t0, "iters": im.iters, "outer": im.outer,
-                            "true_rel_res": im.true_rel_res, "converged": im.converged}
-            PM.close()
-            P64 = fx.Pointing(q_bore, q_det, [ndet], [nsamp], [nside], mode="cache_f64", stream=stream)
-            N64 = fx.Noise.banded(P64, taps)
-            stream.synchronize()
-            t0 = time.perf_counter()
-            x64, _, i64 = fx.mapmaker_cg(P64, N64, d, maxiter=400, tol=1e-8, precision="f64")
-            stream.synchronize()
-            res["fp64"] = {"seconds": time.perf_counter() - t0, "iters": i64.iters, "true_rel_res": i64.true_rel_res,
-                           "converged": i64.converged}
-            res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
-            v = valid
-            res["map_rel_diff"] = float(torch.linalg.norm(xm[v] - x64[v]) / torch.linalg.norm(x64[v]))
-            P64.close()
-        out["cg_to_1e-8"] = res
-
+        out["cg_to_1e-8"] = cg_to_1e8(fx, dev, stream, small=args.small)
     # ---------------- CPU baseline: the FP64 oracle on the host, bounded sample
     if rank == 0 and not args.no_cpu:
         import oracle
