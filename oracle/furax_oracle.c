@@ -388,8 +388,12 @@ void orc_ninv_band(int64_t ndet, int64_t nsamp, int64_t ntaps, const double *tap
 /*
  * M_p = sum_{i: pix[i]=p} w_i ninv[det(i)] w_i^T with w = (1, c, s): the 3x3 diagonal
  * blocks of P^T diag(N^-1) P. Stored as 6 unique entries (00,01,02,11,12,22).
- * Inverse via adjugate / determinant; rcond = 1 / (||M||_1 ||M^-1||_1).
- * valid[p] = hits >= 3 and det > 0 and rcond >= rcond_min; inv = 0 where invalid.
+ * Inverse via the Cholesky factor M = L L^T (backward stable for symmetric positive definite
+ * matrices): M^-1 = L^-T L^-1; rcond = 1 / (||M||_1 ||M^-1||_1).
+ * valid[p] = hits >= 3, every Cholesky pivot > 0 and rcond >= rcond_min; inv = 0 where invalid.
+ * (A block that is singular in exact arithmetic - e.g. a pixel crossed several times with the
+ * same angle - fails a pivot or yields a tiny rcond; an adjugate/determinant inverse of such a
+ * block is rounding noise and can pass an rcond test with an indefinite "inverse".)
  */
 static double orc_norm1_sym(const double *m)
 {
@@ -398,6 +402,35 @@ static double orc_norm1_sym(const double *m)
     double c2 = fabs(m[2]) + fabs(m[4]) + fabs(m[5]);
     double r = c0 > c1 ? c0 : c1;
     return r > c2 ? r : c2;
+}
+
+/* Inverse of the symmetric 3x3 matrix m = (00,01,02,11,12,22) through its Cholesky factor
+ * L (lower): l11 = sqrt(m00), l21 = m01/l11, l31 = m02/l11, l22 = sqrt(m11 - l21^2),
+ * l32 = (m12 - l31 l21)/l22, l33 = sqrt(m22 - l31^2 - l32^2); W = L^-1 by forward substitution;
+ * m^-1 = W^T W. Returns 0 (and leaves inv untouched) if a pivot is not positive. */
+static int orc_bj_invert(const double *m, double *inv)
+{
+    if (!(m[0] > 0.0)) return 0;
+    const double l11 = sqrt(m[0]);
+    const double l21 = m[1] / l11, l31 = m[2] / l11;
+    const double p2 = m[3] - l21 * l21;
+    if (!(p2 > 0.0)) return 0;
+    const double l22 = sqrt(p2);
+    const double l32 = (m[4] - l31 * l21) / l22;
+    const double p3 = (m[5] - l31 * l31) - l32 * l32;
+    if (!(p3 > 0.0)) return 0;
+    const double l33 = sqrt(p3);
+    const double w11 = 1.0 / l11, w22 = 1.0 / l22, w33 = 1.0 / l33;
+    const double w21 = -(l21 * w11) / l22;
+    const double w32 = -(l32 * w22) / l33;
+    const double w31 = -(l31 * w11 + l32 * w21) / l33;
+    inv[0] = (w11 * w11 + w21 * w21) + w31 * w31;
+    inv[1] = w21 * w22 + w31 * w32;
+    inv[2] = w31 * w33;
+    inv[3] = w22 * w22 + w32 * w32;
+    inv[4] = w32 * w33;
+    inv[5] = w33 * w33;
+    return 1;
 }
 
 void orc_bj(int64_t npix, int64_t ndet, int64_t nsamp, const int32_t *pix, const double *cw,
@@ -429,20 +462,9 @@ void orc_bj(int64_t npix, int64_t ndet, int64_t nsamp, const int32_t *pix, const
     for (int64_t p = 0; p < npix; ++p) {
         const double *m = blocks + 6 * p;
         double *v = inv + 6 * p;
-        double a = m[0], b = m[1], c = m[2], d = m[3], e = m[4], f = m[5];
-        /* cofactors of the symmetric matrix [[a,b,c],[b,d,e],[c,e,f]] */
-        double A = d * f - e * e;
-        double B = c * e - b * f;
-        double C = b * e - c * d;
-        double D = a * f - c * c;
-        double E = b * c - a * e;
-        double F = a * d - b * b;
-        double det = a * A + b * B + c * C;
-        int ok = hits[p] >= 3 && det > 0.0;
         double rc = 0.0;
+        int ok = hits[p] >= 3 && orc_bj_invert(m, v);
         if (ok) {
-            v[0] = A / det; v[1] = B / det; v[2] = C / det;
-            v[3] = D / det; v[4] = E / det; v[5] = F / det;
             rc = 1.0 / (orc_norm1_sym(m) * orc_norm1_sym(v));
             ok = rc >= rcond_min;
         }

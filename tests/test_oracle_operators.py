@@ -174,14 +174,71 @@ def test_bj_inverse_spd_and_rcond(orc, hex_small):
     np.linalg.cholesky(M[v])
     rc = 1 / (np.linalg.norm(M[v], 1, axis=(1, 2)) * np.linalg.norm(np.linalg.inv(M[v]), 1, axis=(1, 2)))
     np.testing.assert_allclose(bj["rcond"][v], rc, rtol=1e-9)
-    # the validity rule: at least 3 hits and rcond >= threshold
+    # the validity rule: at least 3 hits, positive definite, rcond >= threshold
     allrc = np.zeros(obs.npix)
     hitm = bj["hits"] >= 3
-    det = np.linalg.det(M)
-    ok = hitm & (det > 0)
+    ok = hitm & (np.linalg.eigvalsh(M)[:, 0] > 0)
     allrc[ok] = 1 / (np.linalg.norm(M[ok], 1, axis=(1, 2)) * np.linalg.norm(np.linalg.inv(M[ok]), 1, axis=(1, 2)))
     assert np.array_equal(v, ok & (allrc >= 1e-3))
     assert np.all(bj["inv"][~v] == 0)
+
+
+def _blocks_from_samples(orc, angles_per_pixel, npix=12):
+    """One detector whose samples visit pixel k at the polarisation angles angles_per_pixel[k]."""
+    pix, c, s = [], [], []
+    for k, angs in enumerate(angles_per_pixel):
+        for a in angs:
+            pix.append(k); c.append(math.cos(2 * a)); s.append(math.sin(2 * a))
+    pix = np.array([pix], np.int32); c = np.array([c]); s = np.array([s])
+    return orc.bj(npix, pix, c, s, orc.Noise(sigma2=np.array([100.0])), rcond_min=1e-3)
+
+
+def test_bj_singular_blocks_are_invalid(orc):
+    """A pixel crossed several times at one angle (or two) has a singular block: it must be
+    excluded, never inverted. Well-spread angles give the textbook inverse."""
+    bj = _blocks_from_samples(orc, [
+        [0.3] * 4,                                   # rank 1
+        [0.1, 0.1, 0.7, 0.7, 0.1],                  # rank 2
+        [0.0, math.pi / 4, math.pi / 2, 3 * math.pi / 4],   # well conditioned: diag(4, 2, 2)/100
+        [0.2, 1.1, 2.3],                             # three distinct angles: rank 3
+        [0.5, 0.5000001, 0.4999999],                 # nearly one angle: rcond far below 1e-3
+    ])
+    assert list(bj["valid"][:5]) == [False, False, True, True, False]
+    idx = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
+    for k in (2, 3):
+        M = bj["blocks"][k][idx]
+        np.testing.assert_allclose(bj["inv"][k][idx], np.linalg.inv(M), rtol=1e-12, atol=1e-14 * np.abs(np.linalg.inv(M)).max())
+    np.testing.assert_allclose(bj["inv"][2][idx], np.diag([100 / 4, 100 / 2, 100 / 2]), rtol=1e-13, atol=1e-12)
+    assert bj["rcond"][4] < 1e-3
+
+
+def test_bj_precession_repeats(orc):
+    """A scan longer than one precession period (72,000 samples at 20 Hz) crosses some pixels
+    only at the same angle, one hour apart: their blocks are singular up to rounding. An inverse
+    through the adjugate/determinant of such a block is noise and can pass an rcond test; the
+    oracle's Cholesky inverse rejects them, and every accepted inverse is positive definite."""
+    o = synth.Observation(256, synth.satellite_scan(160000), synth.hex_focal_plane(4))
+    pix, c, s, _ = orc.pointing(o.nside, o.q_bore, o.q_det)
+    bj = orc.bj(o.npix, pix, c, s, orc.Noise(taps=np.tile(synth.inverse_noise_taps(), (4, 1))), rcond_min=1e-2)
+    idx = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
+    M = bj["blocks"][:, idx]
+    v = bj["valid"]
+    assert np.all(np.linalg.eigvalsh(bj["inv"][v][:, idx])[:, 0] > 0)
+    ev = np.linalg.eigvalsh(M)
+    singular = (bj["hits"] >= 3) & (ev[:, 0] < 1e-12 * ev[:, 2])
+    assert singular.sum() > 0                        # the case occurs in this scan
+    assert not np.any(v & singular)
+    # the adjugate/determinant rule would have accepted some of them with an indefinite inverse
+    a, b_, c_, d, e, f = (bj["blocks"][:, k] for k in range(6))
+    A_, B_, C_ = d * f - e * e, c_ * e - b_ * f, b_ * e - c_ * d
+    det = a * A_ + b_ * B_ + c_ * C_
+    adj = np.stack([A_, B_, C_, a * f - c_ * c_, b_ * c_ - a * e, a * d - b_ * b_], 1)
+    sel = singular & (det > 0)
+    if sel.any():
+        inv_adj = adj[sel] / det[sel, None]
+        rc = 1 / (np.linalg.norm(M[sel], 1, axis=(1, 2)) * np.linalg.norm(inv_adj[:, idx], 1, axis=(1, 2)))
+        fooled = rc >= 1e-2
+        assert fooled.any() and np.any(np.linalg.eigvalsh(inv_adj[fooled][:, idx])[:, 0] < 0)
 
 
 def test_bj_blocks_equal_PT_diag_P(orc, hex_small):
