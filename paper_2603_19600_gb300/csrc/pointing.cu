@@ -280,23 +280,48 @@ __device__ __forceinline__ double norm1_sym(double a, double b, double c, double
     return fmax(c0, fmax(c1, c2));
 }
 
-// In place: m6 holds M on entry and M^-1 (0 where invalid) on exit.
+// Inverse of the symmetric 3x3 block m = (00,01,02,11,12,22) through its Cholesky factor
+// M = L L^T, W = L^-1 by forward substitution, M^-1 = W^T W (explicit round-to-nearest FP64
+// operations, no contraction). Returns false if a pivot is not positive: such a block is not
+// positive definite to working precision (e.g. a pixel crossed only at one angle), and an
+// adjugate/determinant inverse of it would be rounding noise.
+__device__ __forceinline__ bool bj_invert3(const double *m, double *inv)
+{
+    if (!(m[0] > 0.0)) return false;
+    const double l11 = __dsqrt_rn(m[0]);
+    const double l21 = __ddiv_rn(m[1], l11), l31 = __ddiv_rn(m[2], l11);
+    const double p2 = __dsub_rn(m[3], __dmul_rn(l21, l21));
+    if (!(p2 > 0.0)) return false;
+    const double l22 = __dsqrt_rn(p2);
+    const double l32 = __ddiv_rn(__dsub_rn(m[4], __dmul_rn(l31, l21)), l22);
+    const double p3 = __dsub_rn(__dsub_rn(m[5], __dmul_rn(l31, l31)), __dmul_rn(l32, l32));
+    if (!(p3 > 0.0)) return false;
+    const double l33 = __dsqrt_rn(p3);
+    const double w11 = __ddiv_rn(1.0, l11), w22 = __ddiv_rn(1.0, l22), w33 = __ddiv_rn(1.0, l33);
+    const double w21 = -__ddiv_rn(__dmul_rn(l21, w11), l22);
+    const double w32 = -__ddiv_rn(__dmul_rn(l32, w22), l33);
+    const double w31 = -__ddiv_rn(__dadd_rn(__dmul_rn(l31, w11), __dmul_rn(l32, w21)), l33);
+    inv[0] = __dadd_rn(__dadd_rn(__dmul_rn(w11, w11), __dmul_rn(w21, w21)), __dmul_rn(w31, w31));
+    inv[1] = __dadd_rn(__dmul_rn(w21, w22), __dmul_rn(w31, w32));
+    inv[2] = __dmul_rn(w31, w33);
+    inv[3] = __dadd_rn(__dmul_rn(w22, w22), __dmul_rn(w32, w32));
+    inv[4] = __dmul_rn(w32, w33);
+    inv[5] = __dmul_rn(w33, w33);
+    return true;
+}
+
+// In place: m6 holds M on entry and M^-1 (0 where invalid) on exit. Valid iff hits >= 3, the
+// block is positive definite (Cholesky pivots > 0) and rcond = 1/(|M|_1 |M^-1|_1) >= rcond_min.
 __global__ void bj_invert_kernel(double *__restrict__ m6, const int32_t *__restrict__ hits, uint8_t *__restrict__ valid,
                                  double *__restrict__ rcond, int64_t npix, double rcond_min)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
         double *m = m6 + 6 * p;
-        const double a = m[0], b = m[1], c = m[2], d = m[3], e = m[4], f = m[5];
-        // cofactors of [[a,b,c],[b,d,e],[c,e,f]]
-        const double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
-        const double D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
-        const double det = a * A + b * B + c * C;
-        bool ok = hits[p] >= 3 && det > 0.0;
+        double mm[6] = {m[0], m[1], m[2], m[3], m[4], m[5]};
         double rc = 0.0, v[6] = {0, 0, 0, 0, 0, 0};
+        bool ok = hits[p] >= 3 && bj_invert3(mm, v);
         if (ok) {
-            const double id = 1.0 / det;
-            v[0] = A * id; v[1] = B * id; v[2] = C * id; v[3] = D * id; v[4] = E * id; v[5] = F * id;
-            rc = 1.0 / (norm1_sym(a, b, c, d, e, f) * norm1_sym(v[0], v[1], v[2], v[3], v[4], v[5]));
+            rc = 1.0 / (norm1_sym(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5]) * norm1_sym(v[0], v[1], v[2], v[3], v[4], v[5]));
             ok = rc >= rcond_min;
         }
         for (int k = 0; k < 6; ++k) m[k] = ok ? v[k] : 0.0;

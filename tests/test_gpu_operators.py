@@ -210,3 +210,28 @@ def test_mixed_cache_holds_fp64_weights(fx, dev, orc, prob):
     ref = orc.P(opix, oc, os_, m).ravel()
     assert rel(P.apply(torch.as_tensor(m, device=dev), dtype=torch.float64).cpu().numpy(), ref) < 1e-14
     assert rel(P.apply(torch.as_tensor(m, device=dev).float()).cpu().numpy(), ref) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def repeats(orc):
+    """nside 256, 4 detectors x 160,000 samples: longer than one precession period, so some
+    pixels are crossed only at one angle (singular preconditioner blocks)."""
+    o = synth.Observation(256, synth.satellite_scan(160000), synth.hex_focal_plane(4))
+    opix, oc, os_, _ = orc.pointing(o.nside, o.q_bore, o.q_det)
+    taps = np.tile(synth.inverse_noise_taps(), (4, 1))
+    return o, opix, oc, os_, taps
+
+
+@pytest.mark.parametrize("mode", ["cache_f64", "cache_f32"])
+def test_blockdiag_singular_blocks_match_oracle(fx, dev, orc, repeats, mode):
+    o, opix, oc, os_, taps = repeats
+    P = fx.Pointing.from_observations([o], mode=mode, device=dev)
+    bj = fx.blockdiag_precond(P, fx.Noise.banded(P, taps), 1e-2)
+    if mode == "cache_f64":
+        ref = orc.bj(o.npix, opix, oc, os_, orc.Noise(taps=taps), 1e-2)
+        assert np.array_equal(bj["valid"].cpu().numpy(), ref["valid"])
+        v = ref["valid"]
+        assert rel(bj["inv"].cpu().numpy()[v], ref["inv"][v]) < 1e-10
+    v = bj["valid"].cpu().numpy()
+    idx = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
+    assert np.all(np.linalg.eigvalsh(bj["inv"].cpu().numpy()[v][:, idx])[:, 0] > 0)
