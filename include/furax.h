@@ -168,8 +168,9 @@ furax_status furax_noise_inv_apply(const furax_noise_t *n, const void *in, void 
  * ------------------------------------------------------------------------------------- */
 
 /* M_p = sum_{i: pix_i = p} ninv_det(i) w_i w_i^T with w = (1, cos 2psi, sin 2psi) and ninv the
- * diagonal of N^-1 (1/sigma^2, or tap c_0). Inverted in FP64 per pixel (adjugate); pixel p is
- * valid iff hits >= 3, det > 0 and rcond = 1/(|M|_1 |M^-1|_1) >= rcond_min.
+ * diagonal of N^-1 (1/sigma^2, or tap c_0). Inverted in FP64 per pixel through its Cholesky
+ * factor; pixel p is valid iff hits >= 3, every Cholesky pivot is positive (the block is positive
+ * definite to working precision) and rcond = 1/(|M|_1 |M^-1|_1) >= rcond_min.
  * blocks_inv: device FP64 [npix_total][6] = (00,01,02,11,12,22) of M^-1, 0 where invalid;
  * valid: device uint8 [npix_total]; hits: device int32 [npix_total] (may be NULL);
  * rcond: device FP64 [npix_total] (may be NULL). */
