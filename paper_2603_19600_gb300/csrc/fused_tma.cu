@@ -42,7 +42,7 @@ struct TmaSmem {
     float c[kRawStages][kRawN];
     float s[kRawStages][kRawN];
     float xs[kXsStages][XS];
-    float taps[kXsStages][MAXTAPS];
+    alignas(16) float taps[kXsStages][kBandPad];   // band in tap order, c_|j-63|
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
@@ -161,7 +161,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const ObsInfo ob = pv.obs[tl.obs];
             const int64_t gdet = ob.det_off + tl.det;
             const TileSpan sp = tile_span(tl, ob, halo);
-            if (BANDED && tid < MAXTAPS) S.taps[q][tid] = tid < nv.ntaps ? nv.p32[gdet * nv.ntaps + tid] : 0.f;
+            if (BANDED && tid < kBandPad) {
+                const int k = tid < kHalo ? kHalo - tid : tid - kHalo;
+                S.taps[q][tid] = (tid < kBand && k < nv.ntaps) ? nv.p32[gdet * nv.ntaps + k] : 0.f;
+            }
             const int nload = tl.len + 2 * halo;
             const int64_t t_first = tl.t0 - halo;
             const int64_t shift = sp.row + t_first - sp.g0;   // stage index of u is u + shift
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         float y[FR];
         if (ok && base < tl.len) {
             if constexpr (BANDED) {
-                band_product<float, FR>(S.xs[q], S.taps[q], base, y);
+                band_product_x4<FR>(S.xs[q], S.taps[q], base, y);
             } else {
                 const float w = white_scale<float>(nv, gdet);
 #pragma unroll

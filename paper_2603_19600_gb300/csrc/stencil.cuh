@@ -35,4 +35,36 @@ __device__ __forceinline__ void band_product(const T *__restrict__ xs, const T *
     }
 }
 
+// The same sum with the band stored expanded in tap order, T[j] = c_|j-63| for j < 127 and
+// T[127] = 0 (16-byte aligned): four coefficients per 16-byte broadcast load instead of one
+// shared load per tap.
+constexpr int kBandPad = 128;
+
+template <int R>
+__device__ __forceinline__ void band_product_x4(const float *__restrict__ xs, const float *__restrict__ T, int base,
+                                                float (&y)[R])
+{
+    float w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { w[r] = xs[spos(base + r)]; y[r] = 0.f; }
+#pragma unroll
+    for (int j4 = 0; j4 < kBandPad; j4 += 4) {
+        const float4 t4 = *reinterpret_cast<const float4 *>(T + j4);
+        const float tc[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = j4 + jj;
+            if (j < kBand) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r] = fmaf(tc[jj], w[r], y[r]);
+                if (j < kBand - 1) {
+#pragma unroll
+                    for (int r = 0; r < R - 1; ++r) w[r] = w[r + 1];
+                    w[R - 1] = xs[spos(base + R + j)];
+                }
+            }
+        }
+    }
+}
+
 }  // namespace fx
