@@ -31,6 +31,9 @@ import synth  # noqa: E402
 METRIC = "Gsamples/s of P^T N^-1 P apply; CG solve time at residual 1e-8 vs plain FP64 GPU"
 UNIT = "Gsamples/s"
 CG_ITERS = 50
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused_tma_kernel launch on the full
+# 256 x 2^20, nside-512 workload (one ncu capture of the current kernel; profiles/fused_tma_kernel_64det_nside512.md)
+APPLY_DRAM_BYTES = 4.41e9 + 0.5853e9
 
 
 def parse():
@@ -362,7 +365,7 @@ def main():
     apply_ms = f32_ms / f32_n
     achieved = alg_bytes / (apply_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused_tma_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",
+                "traffic": APPLY_DRAM_BYTES if (nside, ndet, nsamp) == (512, 256, 1 << 20) else None, "kernel": "fused_tma_kernel (P^T N^-1 P, FP32 cache, ACC_F32)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": apply_ms, "timed_launches": f32_n,
                 "peak_source": f"{peak_kind} hbm_gbs"}
 
