@@ -42,7 +42,7 @@ struct TmaSmem {
     float c[kRawStages][kRawN];
     float s[kRawStages][kRawN];
     float xs[kXsStages][XS];
-    alignas(16) float taps[kXsStages][kBandPad];   // band in tap order, c_|j-63|
+    alignas(16) float taps[kXsStages][2 * kBandPad];   // band in tap order as (c_|j-63|, c_|j-63|) pairs
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const TileSpan sp = tile_span(tl, ob, halo);
             if (BANDED && tid < kBandPad) {
                 const int k = tid < kHalo ? kHalo - tid : tid - kHalo;
-                S.taps[q][tid] = (tid < kBand && k < nv.ntaps) ? nv.p32[gdet * nv.ntaps + k] : 0.f;
+                const float c = (tid < kBand && k < nv.ntaps) ? nv.p32[gdet * nv.ntaps + k] : 0.f;
+                reinterpret_cast<float2 *>(S.taps[q])[tid] = make_float2(c, c);
             }
             const int nload = tl.len + 2 * halo;
             const int64_t t_first = tl.t0 - halo;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         float y[FR];
         if (ok && base < tl.len) {
             if constexpr (BANDED) {
-                band_product_x4<FR>(S.xs[q], S.taps[q], base, y);
+                band_product_x2(S.xs[q], S.taps[q], base, y);
             } else {
                 const float w = white_scale<float>(nv, gdet);
 #pragma unroll
