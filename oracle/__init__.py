@@ -69,7 +69,7 @@ _SIGS = {
     "orc_phi_batch": (None, [_I, _P, _P, _P]),
     "orc_quat_mul_batch": (None, [_I, _P, _P, _P]),
     "orc_quat_axes_batch": (None, [_I, _P, _P, _P]),
-    "orc_pointing": (_I, [_I, _I, _P, _I, _P, _P, _P, _P, _P]),
+    "orc_pointing": (_I, [_I, _I, _P, _I, _P, _P, _P, _P, _P, _P]),
     "orc_P": (None, [_I, _P, _P, _P, _P, _P]),
     "orc_PT": (None, [_I, _I, _P, _P, _P, _P, _P, _P]),
     "orc_ninv_white": (None, [_I, _I, _P, _P, _P]),
@@ -153,13 +153,16 @@ def pix2ang(nside, pix):
 
 
 # ---------------------------------------------------------------- pointing
-def pointing(nside, q_bore, q_det, psi_offset=None):
-    """Per-sample RING pixel (int32) and weights cos 2psi, sin 2psi (float64), each [ndet][nsamp]."""
+def pointing(nside, q_bore, q_det, psi_offset=None, hwp=None):
+    """Per-sample RING pixel (int32) and weights cos 2psi, sin 2psi (float64), each [ndet][nsamp].
+    With hwp (angle per boresight sample) the weights are cos(4 hwp - 2psi), sin(4 hwp - 2psi)."""
     qb = _c(q_bore, np.float64); qd = _c(q_det, np.float64)
     ns, nd = qb.shape[0], qd.shape[0]
     po = None if psi_offset is None else _c(psi_offset, np.float64)
+    hw = None if hwp is None else _c(hwp, np.float64)
+    assert hw is None or hw.shape == (ns,)
     pix = np.empty((nd, ns), np.int32); c = np.empty((nd, ns)); s = np.empty((nd, ns))
-    bad = lib().orc_pointing(nside, ns, _p(qb), nd, _p(qd), _p(po), _p(pix), _p(c), _p(s))
+    bad = lib().orc_pointing(nside, ns, _p(qb), nd, _p(qd), _p(po), _p(hw), _p(pix), _p(c), _p(s))
     return pix, c, s, int(bad)
 
 
@@ -262,13 +265,17 @@ def pcg(npix, pix, c, s, noise: Noise, valid, minv, b, maxiter, tol=1e-8):
     return x, int(it), hist[: it + 1]
 
 
-def chi2_grad(npix, pix, c, s, noise: Noise, m, d, want_grad=True):
+def chi2_grad(npix, pix, c, s, noise: Noise, m, d, want_grad=True, hwp=False):
+    """chi^2 and its gradients. With an ideal half-wave plate (hwp=True) the weights are
+    cos(4w - 2psi - 2delta), sin(...): their derivative in delta is minus the one without it."""
     pix = _c(pix, np.int32); c = _c(c, np.float64); s = _c(s, np.float64)
     m = _c(m, np.float64); d = _c(d, np.float64)
     gm = np.empty((npix, 3)) if want_grad else None
     gp = np.empty(pix.shape[0]) if want_grad else None
     chi2 = lib().orc_chi2_grad(npix, pix.shape[0], pix.shape[1], _p(pix), _p(c), _p(s),
                                *_noise_args(noise), _p(m), _p(d), _p(gm), _p(gp))
+    if want_grad and hwp:
+        gp = -gp
     return chi2, gm, gp
 
 

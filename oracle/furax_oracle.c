@@ -263,7 +263,7 @@ void orc_quat_axes_batch(int64_t n, const double *q, double *d, double *o)
  * A non-finite quaternion gives pixel -1 and weights 0. Returns the number of such samples.
  */
 int64_t orc_pointing(int64_t nside, int64_t nsamp, const double *q_bore, int64_t ndet,
-                     const double *q_det, const double *psi_offset,
+                     const double *q_det, const double *psi_offset, const double *hwp,
                      int32_t *pix, double *cw, double *sw)
 {
     int64_t bad = 0;
@@ -291,6 +291,15 @@ int64_t orc_pointing(int64_t nside, int64_t nsamp, const double *q_bore, int64_t
             if (psi_offset) {
                 double c1 = c * c2d - s * s2d;
                 double s1 = s * c2d + c * s2d;
+                c = c1; s = s1;
+            }
+            if (hwp) {
+                /* Ideal half-wave plate at angle w in front of the detector (HWPOperator, Table 3):
+                 * the detector's angle 2psi' enters as 4w - 2psi', i.e.
+                 * (cos(4w - 2psi'), sin(4w - 2psi')) = (cos4w c + sin4w s, sin4w c - cos4w s). */
+                double c4 = cos(4.0 * hwp[t]), s4 = sin(4.0 * hwp[t]);
+                double c1 = c4 * c + s4 * s;
+                double s1 = s4 * c - c4 * s;
                 c = c1; s = s1;
             }
             cw[i] = c; sw[i] = s;

@@ -68,6 +68,13 @@ def satellite_scan(nsamp: int, fsamp: float = FSAMP_HZ, spin_rpm: float = 1.0,
     return _wxyz(r)
 
 
+def hwp_angle(nsamp: int, fsamp: float = FSAMP_HZ, hwp_rpm: float = 46.0, t0: float = 0.0,
+              omega0: float = 0.0) -> np.ndarray:
+    """Angle of a continuously rotating half-wave plate, omega(t) = omega0 + 2 pi (rpm / 60) t."""
+    t = t0 + np.arange(nsamp, dtype=np.float64) / fsamp
+    return omega0 + 2.0 * math.pi * (hwp_rpm / 60.0) * t
+
+
 def copointed_detectors(psi_deg) -> np.ndarray:
     """Detectors on the boresight, each rotated by its polarisation angle: q_det = Rz(psi)."""
     psi = np.radians(np.asarray(psi_deg, dtype=np.float64))
@@ -168,6 +175,7 @@ class Observation:
     q_bore: np.ndarray           # [nsamp][4] float64 (w, x, y, z)
     q_det: np.ndarray            # [ndet][4] float64
     psi_offset: np.ndarray | None = None  # [ndet] rad
+    hwp: np.ndarray | None = None         # [nsamp] half-wave-plate angle (rad) per boresight sample
 
     @property
     def ndet(self) -> int:
