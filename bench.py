@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cg1e8", action="store_true", help="skip the solve-to-1e-8 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-hwp", action="store_true", help="skip the step timing with a half-wave plate")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the fused P^T N^-1 P apply (profiling runs; not a bench line)")
     ap.add_argument("--ndet", type=int, default=None, help="override the detector count (profiling runs)")
@@ -243,6 +244,36 @@ def cg_to_1e8(fx, dev, stream, wl, q_bore, q_det, d):
     return res
 
 
+def hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps: int):
+    """The same solver step with an ideal half-wave plate rotating at 46 rpm in front of every
+    detector (weights cos(4w - 2psi), sin(4w - 2psi)): the plate is applied while the pointing
+    cache is filled, so the iteration itself is unchanged."""
+    import torch
+    nside, nd, ns = wl["nside"], wl["ndet"], wl["nsamp"]
+    S = nd * ns
+    w = torch.from_numpy(synth.hwp_angle(ns)).to(dev)
+    with torch.cuda.stream(stream):
+        P = fx.Pointing(q_bore, q_det, [nd], [ns], [nside], mode="cache_f32", stream=stream, hwp_angle=w)
+        N = fx.Noise.banded(P, taps)
+
+        def step():
+            P.refresh()
+            return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=0.0,
+                                  max_outer=1, true_residual=False, check_every=10)
+        step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+        P.close()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_step": ms, "value": S * CG_ITERS / (ms / 1e3) / 1e9, "unit": UNIT, "steps": steps,
+            "workload": "same scan, ideal half-wave plate at 46 rpm"}
+
+
 def _wl_name(wl):
     return (f"satellite scan, {wl['ndet']} detectors (hex focal plane, radius 5 deg) x {wl['nsamp']} samples, "
             f"HEALPix nside {wl['nside']}, 1/f + white noise, 64-tap banded N^-1, {CG_ITERS} PCG iterations")
@@ -407,6 +438,9 @@ def main():
         out["e2e"] = {"value": job_value(samples_per_step, args.steps, e2e_ms, world), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
 
+    # ---------------- the same step with a half-wave plate (HWP-modulated pointing)
+    if not args.no_hwp:
+        out["hwp"] = hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps=max(1, min(args.steps, 3)))
     # ---------------- solve to a true residual of 1e-8 on the same workload: mixed vs plain FP64
     if rank == 0 and not args.no_cg1e8 and world == 1:
         out["cg_to_1e-8"] = cg_to_1e8(fx, dev, stream, wl, q_bore, q_det, d)

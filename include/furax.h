@@ -90,6 +90,11 @@ typedef struct {
     const double *q_bore;     /* device [sum nsamp][4], unit quaternions (not renormalised) */
     const double *q_det;      /* device [sum ndet][4], unit quaternions */
     const double *psi_offset; /* device [sum ndet] polarisation-angle offsets (rad), or NULL */
+    const double *hwp_angle;  /* device [sum nsamp] angle w (rad) of an ideal half-wave plate in front
+                                 of every detector, one value per boresight sample, or NULL (no plate).
+                                 With a plate (HWPOperator, Table 3) the weights become
+                                 (1, cos(4w - 2psi), sin(4w - 2psi)); pixels do not change. Read once
+                                 at creation (kept as cos 4w, sin 4w). */
 } furax_obs_desc;
 
 /* ---------------------------------------------------------------------------------------
@@ -116,7 +121,10 @@ furax_status furax_pointing_info(const furax_pointing_t *p, int64_t *nsamp_total
 furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream);
 
 /* Replace the per-detector polarisation-angle offsets (device [sum ndet] rad, or NULL for none).
- * Weights become (cos 2(psi+delta), sin 2(psi+delta)); pixels do not change. */
+ * Weights become (cos 2(psi+delta), sin 2(psi+delta)), or with a half-wave plate
+ * (cos(4w - 2(psi+delta)), sin(4w - 2(psi+delta))) - the offset rotation passes through the plate
+ * with its sign reversed ("Algebraic reductions": R(theta) o HWP = HWP o R(-theta)); pixels do
+ * not change. */
 furax_status furax_pointing_set_psi_offset(furax_pointing_t *p, const double *psi_offset, void *stream);
 
 /* Expand the pointing: per sample its pixel within its observation's map (int32, -1 if

@@ -247,7 +247,7 @@ static void pointing_free(furax_pointing *p)
 {
     if (!p) return;
     destroy_cg_ws(p);
-    cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs);
+    cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs); cudaFree(p->d_hwp_cs);
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
     cudaFree(p->c32lo); cudaFree(p->s32lo); cudaFree(p->ws_bore_m);
     cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc_lo); cudaFree(p->ws_acc64); cudaFree(p->ws_df_lo); cudaFree(p->ws_x64);
@@ -297,6 +297,8 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
     p->q_det = desc->q_det;
     Layout L;
     build_layout(desc, L);
+    if (desc->hwp_angle)
+        for (auto &o : L.obs) o.hwp = 1;
     p->obs = L.obs; p->tiles = L.tiles; p->ptiles = L.ptiles;
     p->ndet_total = L.ndet; p->nbore_total = L.nbore; p->nsamp_total = L.nsamp; p->npix_total = L.npix;
     p->max_ndet = L.max_ndet;
@@ -320,6 +322,13 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
         (rc = check_cuda(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), st), "memset"))) {
         pointing_free(p);
         return rc;
+    }
+    if (desc->hwp_angle) {   // before the offsets: they pass through the plate
+        if (!is_device_ptr(desc->hwp_angle)) {
+            pointing_free(p);
+            return set_error(FURAX_EINVAL, "hwp_angle must be device memory");
+        }
+        if ((rc = launch_set_hwp(p, desc->hwp_angle, st))) { pointing_free(p); return rc; }
     }
     if (desc->psi_offset) {
         REQUIRE(is_device_ptr(desc->psi_offset), "psi_offset must be device memory");

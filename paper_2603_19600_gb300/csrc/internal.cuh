@@ -26,7 +26,7 @@ struct ObsInfo {
     int32_t nptile;    // number of pixel tiles
     int32_t ndet;
     int32_t nside;
-    int32_t pad;
+    int32_t hwp;       // 1 if the batch has a half-wave plate (weights reflected per sample)
 };
 
 struct Tile {          // one detector, samples [t0, t0+len)
@@ -53,6 +53,7 @@ struct PointingView {
     const float *c32, *s32; // cache modes 1 and 3 (weights rounded to FP32)
     const float *c32lo, *s32lo; // cache mode 3: FP64 weight - FP32 weight
     const double *c64, *s64;// cache mode 2
+    const double2 *hwp_cs;  // per boresight sample (cos 4w, sin 4w) of the half-wave plate, or nullptr
 };
 
 struct NoiseView {
@@ -109,6 +110,8 @@ struct furax_pointing {
     const double *q_bore = nullptr, *q_det = nullptr;
     double2 *d_psi_cs = nullptr;
     bool has_psi = false;
+    double2 *d_hwp_cs = nullptr;      // [nbore] (cos 4w, sin 4w), with a half-wave plate
+    bool has_hwp = false;
     int32_t *pix = nullptr;
     float *c32 = nullptr, *s32 = nullptr;
     float *c32lo = nullptr, *s32lo = nullptr;
@@ -130,7 +133,8 @@ struct furax_pointing {
     float *ws_bore_m = nullptr;       // [nbore][18] boresight rotation matrices (double-FP32)
     fx::CgWs *cg = nullptr;           // solver workspace (allocated by the first solve)
     fx::PointingView view() const {
-        return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c32lo, s32lo, c64, s64};
+        return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c32lo, s32lo, c64, s64,
+                                has_hwp ? d_hwp_cs : nullptr};
     }
 };
 
@@ -157,6 +161,7 @@ furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, fl
                            double *s64, unsigned long long *n_invalid, cudaStream_t st, bool all_mode,
                            float *c32lo = nullptr, float *s32lo = nullptr);
 furax_status launch_set_psi(furax_pointing *p, const double *psi, cudaStream_t st);
+furax_status launch_set_hwp(furax_pointing *p, const double *hwp, cudaStream_t st);
 // FP32 cache fill with certified FP32 pixels and exact FP64 fallback (pointing_fast.cu)
 furax_status launch_expand_fast(const furax_pointing *p, unsigned long long *n_invalid, cudaStream_t st);
 furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void *tod, int tod_t, cudaStream_t st);

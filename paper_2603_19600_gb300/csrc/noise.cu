@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(FT) chi2_kernel(const Tile *__restrict__ tiles
     __syncthreads();
 
     double part_chi2 = 0.0, part_psi = 0.0;
+    // d(weights)/d delta = 2 (-s, c), or its opposite when a half-wave plate reflects the weights
+    const double psi_sign = ob.hwp ? -1.0 : 1.0;
     const int base = threadIdx.x * FR;
     if (base < tl.len) {
         T y[FR];
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(FT) chi2_kernel(const Tile *__restrict__ tiles
             const double c = (double)sc[spos(k)], s = (double)ss[spos(k)];
             const int64_t gp = ob.map_off + pix;
             const double *mm = m + 3 * gp;
-            part_psi += nr * 2.0 * (mm[2] * c - mm[1] * s);
+            part_psi += nr * 2.0 * (mm[2] * c - mm[1] * s) * psi_sign;
             if (grad_map) {
                 red_add_f64(grad_map + 3 * gp + 0, -2.0 * nr);
                 red_add_f64(grad_map + 3 * gp + 1, -2.0 * nr * c);

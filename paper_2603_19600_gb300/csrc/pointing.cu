@@ -16,7 +16,8 @@ namespace fx {
 template <typename WT>
 __global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                      const double *__restrict__ q_bore, const double *__restrict__ q_det,
-                                                     const double2 *__restrict__ psi_cs, int32_t *__restrict__ pix_out,
+                                                     const double2 *__restrict__ psi_cs, const double2 *__restrict__ hwp_cs,
+                                                     int32_t *__restrict__ pix_out,
                                                      WT *__restrict__ c_out, WT *__restrict__ s_out,
                                                      unsigned long long *__restrict__ n_invalid,
                                                      float *__restrict__ c_lo, float *__restrict__ s_lo)
@@ -31,6 +32,7 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tile *__restrict__ ti
         const int64_t t = tl.t0 + k;
         SampleF64 r = point_f64(load_quat(q_bore, ob.bore_off + t), qd, ob.nside);
         double c = r.c, s = r.s;
+        if (hwp_cs && r.pix >= 0) apply_hwp<double>(c, s, hwp_cs[ob.bore_off + t]);
         if (psi_cs && r.pix >= 0) rotate_psi<double>(c, s, cs);
         const int64_t i = ob.tod_off + tl.det * ob.nsamp + t;
         pix_out[i] = r.pix;
@@ -52,31 +54,56 @@ furax_status launch_expand(const furax_pointing *p, int32_t *pix, float *c32, fl
 {
     if (p->n_tiles == 0) return FURAX_OK;
     const double2 *cs = p->has_psi ? p->d_psi_cs : nullptr;
+    const double2 *hw = p->has_hwp ? p->d_hwp_cs : nullptr;
     if (c64 || (!c32 && !c64))
-        expand_kernel<double><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
-                                                                    c64, s64, n_invalid, nullptr, nullptr);
+        expand_kernel<double><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, hw,
+                                                                    pix, c64, s64, n_invalid, nullptr, nullptr);
     else
-        expand_kernel<float><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, pix,
-                                                                   c32, s32, n_invalid, c32lo, s32lo);
+        expand_kernel<float><<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, cs, hw,
+                                                                   pix, c32, s32, n_invalid, c32lo, s32lo);
     count_launches(1);
     return check_launch("pointing expansion");
 }
 
-__global__ void psi_kernel(const double *__restrict__ psi, double2 *__restrict__ cs, int64_t n)
+// (cos 2 delta, sin 2 delta) per detector; with a half-wave plate the rotation is applied to
+// weights that already carry the plate, where it acts with the opposite sign (see apply_hwp).
+__global__ void psi_kernel(const double *__restrict__ psi, double2 *__restrict__ cs, int64_t n, int through_hwp)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) {
         double s, c;
         sincos(2.0 * psi[i], &s, &c);
+        cs[i] = make_double2(c, through_hwp ? -s : s);
+    }
+}
+
+// (cos 4w, sin 4w) per boresight sample of the half-wave plate angle w.
+__global__ void hwp_kernel(const double *__restrict__ w, double2 *__restrict__ cs, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s, c;
+        sincos(4.0 * w[i], &s, &c);
         cs[i] = make_double2(c, s);
     }
+}
+
+furax_status launch_set_hwp(furax_pointing *p, const double *hwp, cudaStream_t st)
+{
+    if (!hwp) { p->has_hwp = false; return FURAX_OK; }
+    furax_status rc = ensure_ws(p, (void **)&p->d_hwp_cs, sizeof(double2) * std::max<int64_t>(1, p->nbore_total));
+    if (rc) return rc;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 152 * 16));
+    hwp_kernel<<<g, 256, 0, st>>>(hwp, p->d_hwp_cs, p->nbore_total);
+    count_launches(1);
+    p->has_hwp = true;
+    return check_launch("half-wave plate angles");
 }
 
 furax_status launch_set_psi(furax_pointing *p, const double *psi, cudaStream_t st)
 {
     if (!psi) { p->has_psi = false; return FURAX_OK; }
     int64_t n = p->ndet_total;
-    psi_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, p->d_psi_cs, n);
+    psi_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, p->d_psi_cs, n, p->has_hwp ? 1 : 0);
     count_launches(1);
     p->has_psi = true;
     return check_launch("psi offsets");

@@ -132,7 +132,8 @@ __device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, in
 
 __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                           const double *__restrict__ q_bore, const double *__restrict__ q_det,
-                                                          const float *__restrict__ bm, int32_t *__restrict__ pix_out,
+                                                          const float *__restrict__ bm, const double2 *__restrict__ hwp_cs,
+                                                          int32_t *__restrict__ pix_out,
                                                           float *__restrict__ c_out, float *__restrict__ s_out,
                                                           unsigned long long *__restrict__ n_invalid)
 {
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict
                 const float inv = 1.f / n2;
                 c = (a * a - b * b) * inv;
                 s = 2.f * a * b * inv;
+                if (hwp_cs) apply_hwp<float>(c, s, hwp_cs[ob.bore_off + t]);
             }
         }
         if (ok) {
@@ -203,9 +205,11 @@ __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
         const int64_t t = tl.t0 + queue[j];
         const SampleF64 r = point_f64(load_quat(q_bore, ob.bore_off + t), qd, ob.nside);
+        double c = r.c, s = r.s;
+        if (hwp_cs && r.pix >= 0) apply_hwp<double>(c, s, hwp_cs[ob.bore_off + t]);
         pix_out[row + t] = r.pix;
-        c_out[row + t] = (float)r.c;
-        s_out[row + t] = (float)r.s;
+        c_out[row + t] = (float)c;
+        s_out[row + t] = (float)s;
         bad += r.pix < 0;
     }
     if (n_invalid) {
@@ -226,7 +230,8 @@ furax_status launch_expand_fast(const furax_pointing *p, unsigned long long *n_i
     if ((rc = check_launch("boresight matrices"))) return rc;
     if (p->n_tiles == 0) return FURAX_OK;
     expand_fast_kernel<<<(unsigned)p->n_tiles, 256, 0, st>>>(p->d_tiles, p->d_obs, p->q_bore, p->q_det, pm->ws_bore_m,
-                                                             p->pix, p->c32, p->s32, n_invalid);
+                                                             p->has_hwp ? p->d_hwp_cs : nullptr, p->pix, p->c32,
+                                                             p->s32, n_invalid);
     count_launches(1);
     return check_launch("fast pointing expansion");
 }

@@ -182,6 +182,21 @@ __device__ __forceinline__ void rotate_psi(T &c, T &s, double2 cs)
     c = c1; s = s1;
 }
 
+// Ideal half-wave plate at angle w in front of the detector (HWPOperator, Table 3 of the Furax
+// paper): the detector's angle enters the weights as 4w - 2psi, i.e. (cos 2psi, sin 2psi) is
+// reflected into (cos 4w c + sin 4w s, sin 4w c - cos 4w s). An offset rotation by 2 delta applied
+// before the plate equals a rotation by -2 delta after it ("Algebraic reductions":
+// R(theta) o HWP = HWP o R(-theta)), which is how per-detector offsets are applied to weights
+// that already carry the plate (see launch_set_psi).
+template <typename T>
+__device__ __forceinline__ void apply_hwp(T &c, T &s, double2 h)
+{
+    const T c4 = (T)h.x, s4 = (T)h.y;
+    const T c1 = c4 * c + s4 * s;
+    const T s1 = s4 * c - c4 * s;
+    c = c1; s = s1;
+}
+
 // Per-sample pointing from a PointingView, for each storage mode.
 // MODE 0: on the fly (FP64); 1: FP32 cache; 2: FP64 cache; 3: FP32 hi + lo cache (FP32 readers see
 // hi, FP64 readers hi + lo). Returns the pixel local to the
@@ -195,12 +210,12 @@ __device__ __forceinline__ int32_t get_sample(const PointingView &pv, const ObsI
     if constexpr (MODE == 0) {
         SampleF64 r = point_f64(load_quat(pv.q_bore, ob.bore_off + t), load_quat(pv.q_det, gdet), ob.nside);
         pix = r.pix;
-        c = (T)r.c; s = (T)r.s;
-        if (pv.psi_cs && pix >= 0) {
-            double cc = r.c, ss = r.s;
-            rotate_psi<double>(cc, ss, pv.psi_cs[gdet]);
-            c = (T)cc; s = (T)ss;
+        double cc = r.c, ss = r.s;
+        if (pix >= 0) {
+            if (pv.hwp_cs) apply_hwp<double>(cc, ss, pv.hwp_cs[ob.bore_off + t]);
+            if (pv.psi_cs) rotate_psi<double>(cc, ss, pv.psi_cs[gdet]);
         }
+        c = (T)cc; s = (T)ss;
         return pix;
     } else {
         const int64_t i = ob.tod_off + det * ob.nsamp + t;

@@ -26,16 +26,21 @@ class Pointing:
     q_bore: float64 [sum nsamp][4] (w, x, y, z); q_det: float64 [sum ndet][4]; both on the GPU
     and kept alive by this object. mode: "cache_f32" (pixel + FP32 weights cached, 12 B/sample),
     "cache_f64" (20 B/sample) or "on_the_fly" (recomputed from the quaternions each call).
+    hwp_angle: optional float64 [sum nsamp] angle of an ideal half-wave plate per boresight sample
+    (weights become cos(4w - 2psi), sin(4w - 2psi)); read once here.
     """
 
-    def __init__(self, q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode="cache_f32", stream=None):
+    def __init__(self, q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode="cache_f32", stream=None,
+                 hwp_angle=None):
         self.ndet, self.nsamp, self.nside = [list(map(int, v)) for v in (ndet, nsamp, nside)]
         self.q_bore = q_bore.contiguous()
         self.q_det = q_det.contiguous()
         self.mode = mode
         self.handle = None
+        self.has_hwp = hwp_angle is not None
         self.handle = nat.furax_pointing_create(self.q_bore, self.q_det, self.ndet, self.nsamp, self.nside,
-                                                psi_offset, _MODES[mode], stream)
+                                                psi_offset, _MODES[mode], stream,
+                                                None if hwp_angle is None else hwp_angle.contiguous())
         info = nat.furax_pointing_info(self.handle)
         self.nsamp_total = info["nsamp_total"]
         self.npix_total = info["npix_total"]
@@ -52,8 +57,14 @@ class Pointing:
         if any(getattr(o, "psi_offset", None) is not None for o in observations):
             psi = torch.cat([torch.as_tensor(o.psi_offset if o.psi_offset is not None else [0.0] * o.ndet)
                              for o in observations]).to(device, torch.float64)
+        hw = [getattr(o, "hwp", None) for o in observations]
+        if any(h is not None for h in hw) and any(h is None for h in hw):
+            raise ValueError("either every observation has a half-wave plate angle stream or none has")
+        hwp = None
+        if hw[0] is not None:
+            hwp = torch.cat([torch.as_tensor(h) for h in hw]).to(device, torch.float64)
         return cls(qb, qd, [o.q_det.shape[0] for o in observations], [o.q_bore.shape[0] for o in observations],
-                   [o.nside for o in observations], psi, mode, stream)
+                   [o.nside for o in observations], psi, mode, stream, hwp)
 
     def close(self):
         if self.handle:
