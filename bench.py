@@ -33,7 +33,7 @@ UNIT = "Gsamples/s"
 CG_ITERS = 50
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_tma_kernel launch on the full
 # 256 x 2^20, nside-512 workload (one ncu capture of the current kernel; profiles/fused_tma_kernel_64det_nside512.md)
-APPLY_DRAM_BYTES = 4.41e9 + 0.5853e9
+APPLY_DRAM_BYTES = 4.48e9 + 0.6347e9
 
 
 def parse():
