@@ -197,6 +197,91 @@ __device__ __forceinline__ void band_product_dfx(const float *__restrict__ xs, c
     }
 }
 
+// Packed form of the same compensated sum on output pairs (y_i, y_{i+8}): every step is the
+// lane-wise f32x2 version of dot2_step_x, with the product negated once so that no packed
+// negation is needed (fl(-ch x) = -fl(ch x), S - (-p) = S + p, -((-p) + b) = p - b exactly), so
+// the results are bit-identical with half the instructions. C4[j] = (c_hi, c_hi, -c_hi, -c_hi) and
+// CL2[j] = (c_lo, c_lo) hold the band in tap order (j < 127; zero for j = 127).
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ void dot2_step_x2(unsigned long long ch, unsigned long long nch, unsigned long long cl,
+                                             unsigned long long x, unsigned long long &S, unsigned long long &E)
+{
+    const unsigned long long np = f2_mul(nch, x);          // -p
+    const unsigned long long e = f2_fma(ch, x, np);        // ch x - p exactly
+    const unsigned long long s = f2_sub(S, np);            // S + p
+    const unsigned long long bv = f2_sub(s, S);
+    const unsigned long long t2 = f2_sub(S, f2_sub(s, bv));
+    const unsigned long long err = f2_sub(t2, f2_add(np, bv));   // (S - (s - bv)) + (p - bv)
+    S = s;
+    E = f2_fma(cl, x, f2_add(E, f2_add(err, e)));
+}
+
+template <int R>
+__device__ __forceinline__ void band_product_dfx2(const float *__restrict__ xs, const float4 *__restrict__ C4,
+                                                  const float2 *__restrict__ CL2, int base, float (&S)[R], float (&E)[R])
+{
+    constexpr int H = R / 2;
+    unsigned long long W[H], SS[H], EE[H];   // W[i] = (x[base+i+j], x[base+i+H+j]) at tap j
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        W[i] = pack_f32x2(xs[spos(base + i)], xs[spos(base + i + H)]);
+        SS[i] = 0ull;
+        EE[i] = 0ull;
+    }
+#pragma unroll 1
+    for (int j0 = 0; j0 < kBandPad; j0 += kDfJB) {
+#pragma unroll
+        for (int jj = 0; jj < kDfJB; ++jj) {
+            const int j = j0 + jj;
+            if (j < kBand) {
+                const float4 c4 = C4[j];
+                const float2 c2 = CL2[j];
+                const unsigned long long ch = pack_f32x2(c4.x, c4.y), nch = pack_f32x2(c4.z, c4.w);
+                const unsigned long long cl = pack_f32x2(c2.x, c2.y);
+#pragma unroll
+                for (int i = 0; i < H; ++i) dot2_step_x2(ch, nch, cl, W[i], SS[i], EE[i]);
+                if (j < kBand - 1) {
+                    float lo0, hi0;
+                    unpack_f32x2(W[0], lo0, hi0);
+                    const unsigned long long wl = pack_f32x2(hi0, xs[spos(base + R + j)]);
+#pragma unroll
+                    for (int i = 0; i < H - 1; ++i) W[i] = W[i + 1];
+                    W[H - 1] = wl;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        unpack_f32x2(SS[i], S[i], S[i + H]);
+        unpack_f32x2(EE[i], E[i], E[i + H]);
+    }
+}
+
 // binary32 -> binary64 from the IEEE 754 encodings: sign kept, exponent rebiased by
 // 1023 - 127 = 896, significand shifted into the top of the 52-bit field. Exact for normal
 // numbers and zeros; subnormals, infinities and NaNs take the hardware conversion.
@@ -234,7 +319,8 @@ __device__ __forceinline__ int32_t sample_df(const PointingView &pv, const ObsIn
     return pix;
 }
 
-constexpr size_t kDfRhsSmem = sizeof(float) * (XS + CS + 2 * MAXTAPS);
+constexpr size_t kDfRhsSmem = sizeof(float4) * kBandPad + sizeof(float2) * kBandPad + sizeof(float) * (XS + CS + 2 * MAXTAPS);
+static_assert(sizeof(float4) * kBandPad % 16 == 0 && sizeof(float2) * kBandPad % 16 == 0, "coefficient arrays stay 16-byte aligned");
 
 template <int MODE, bool BANDED>
 __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
@@ -242,7 +328,9 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
                                                        float4 *__restrict__ acc_lo)
 {
     extern __shared__ __align__(16) float rsm[];
-    float *xs = rsm;            // [XS] d over the tile and its halos; then y_hi of the core samples
+    float4 *C4 = reinterpret_cast<float4 *>(rsm);            // [kBandPad] (c_hi, c_hi, -c_hi, -c_hi), tap order
+    float2 *CL2 = reinterpret_cast<float2 *>(C4 + kBandPad); // [kBandPad] (c_lo, c_lo)
+    float *xs = reinterpret_cast<float *>(CL2 + kBandPad);   // [XS] d over the tile and halos; then y_hi of the core
     float *yl = xs + XS;        // [CS] y_lo of the core samples
     float *th = yl + CS;        // [MAXTAPS]
     float *tl = th + MAXTAPS;   // [MAXTAPS]
@@ -257,6 +345,13 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
         else c = threadIdx.x == 0 ? nv.p64[gdet] : 0.0;
         split_df(c, th[threadIdx.x], tl[threadIdx.x]);
     }
+    if (BANDED && threadIdx.x < kBandPad) {
+        const int j = threadIdx.x, k = j < kHalo ? kHalo - j : j - kHalo;
+        float h = 0.f, l = 0.f;
+        if (j < kBand && k < nv.ntaps) split_df(nv.p64[gdet * nv.ntaps + k], h, l);
+        C4[j] = make_float4(h, h, -h, -h);
+        CL2[j] = make_float2(l, l);
+    }
     const int nload = tile.len + 2 * halo;
     const int64_t row = ob.tod_off + tile.det * ob.nsamp;
     for (int u = threadIdx.x; u < nload; u += FT) {
@@ -269,7 +364,7 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
     float S[FR], E[FR];
     if (base < tile.len) {
         if constexpr (BANDED) {
-            band_product_dfx<FR>(xs, th, tl, base, S, E);
+            band_product_dfx2<FR>(xs, C4, CL2, base, S, E);
         } else {
 #pragma unroll
             for (int r = 0; r < FR; ++r) {

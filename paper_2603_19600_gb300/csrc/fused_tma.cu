@@ -29,6 +29,7 @@ namespace fx {
 
 constexpr int kTmaGather = 7;                      // gather warps
 constexpr int kTmaConsumer = 8;                    // consumer warps
+constexpr int kConsOut = TILE / (32 * kTmaConsumer);   // consecutive outputs per consumer thread
 constexpr int kTmaThreads = 32 * (kTmaGather + kTmaConsumer + 1);
 constexpr int kRawStages = 2;
 constexpr int kXsStages = 2;
@@ -209,15 +210,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const Tile tl = tiles[ti];
         const ObsInfo ob = pv.obs[tl.obs];
         const int64_t gdet = ob.det_off + tl.det;
-        const int base = tid * FR;
-        float y[FR];
+        const int base = tid * kConsOut;
+        float y[kConsOut];
         if (ok && base < tl.len) {
             if constexpr (BANDED) {
-                band_product_x2(S.xs[q], S.taps[q], base, y);
+                band_product_x2<kConsOut>(S.xs[q], S.taps[q], base, y);
             } else {
                 const float w = white_scale<float>(nv, gdet);
 #pragma unroll
-                for (int i = 0; i < FR; ++i) y[i] = S.xs[q][spos(base + i)] * w;
+                for (int i = 0; i < kConsOut; ++i) y[i] = S.xs[q][spos(base + i)] * w;
             }
         }
         // Every consumer has read its stencil inputs: y overwrites the stage in place (core
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (!consumers_all(ok)) break;
         float *ys = S.xs[q];
 #pragma unroll
-        for (int i = 0; i < FR; ++i)
+        for (int i = 0; i < kConsOut; ++i)
             if (base + i < tl.len) ys[spos(base + i)] = y[i];
         consumers_sync();
         const TileSpan sp = tile_span(tl, ob, halo);
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         double2 cs = make_double2(1.0, 0.0);
         if (pv.psi_cs) cs = pv.psi_cs[gdet];
 #pragma unroll 4
-        for (int k = 0; k < FR; ++k) {
+        for (int k = 0; k < kConsOut; ++k) {
             const int u = tid + k * 32 * kTmaConsumer;
             if (u >= tl.len) break;
             const int32_t pix = S.pix[r][u + shift];

@@ -59,14 +59,17 @@ __device__ __forceinline__ void fma_f32x2(unsigned long long &d, unsigned long l
     asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
-// 16 consecutive outputs per thread: y[r] = sum_j c_|j-63| x[base + r + j] (x in skewed slots).
+// R consecutive outputs per thread (R even): y[r] = sum_j c_|j-63| x[base + r + j] (x in skewed
+// slots), accumulated as pairs (y_i, y_{i+R/2}).
+template <int R>
 __device__ __forceinline__ void band_product_x2(const float *__restrict__ xs, const float *__restrict__ T2, int base,
-                                                float (&y)[16])
+                                                float (&y)[R])
 {
-    unsigned long long W[8], Y[8];   // W[i] = (x[base+i+j], x[base+i+8+j]) at tap j
+    constexpr int H = R / 2;
+    unsigned long long W[H], Y[H];   // W[i] = (x[base+i+j], x[base+i+H+j]) at tap j
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        W[i] = pack_f32x2(xs[spos(base + i)], xs[spos(base + i + 8)]);
+    for (int i = 0; i < H; ++i) {
+        W[i] = pack_f32x2(xs[spos(base + i)], xs[spos(base + i + H)]);
         Y[i] = 0ull;
     }
 #pragma unroll
@@ -78,20 +81,20 @@ __device__ __forceinline__ void band_product_x2(const float *__restrict__ xs, co
             const int j = j2 + jj;
             if (j < kBand) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) fma_f32x2(Y[i], W[i], cpair[jj]);
+                for (int i = 0; i < H; ++i) fma_f32x2(Y[i], W[i], cpair[jj]);
                 if (j < kBand - 1) {
                     float lo0, hi0;
                     unpack_f32x2(W[0], lo0, hi0);
-                    const unsigned long long w7 = pack_f32x2(hi0, xs[spos(base + 16 + j)]);
+                    const unsigned long long wl = pack_f32x2(hi0, xs[spos(base + R + j)]);
 #pragma unroll
-                    for (int i = 0; i < 7; ++i) W[i] = W[i + 1];
-                    W[7] = w7;
+                    for (int i = 0; i < H - 1; ++i) W[i] = W[i + 1];
+                    W[H - 1] = wl;
                 }
             }
         }
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) unpack_f32x2(Y[i], y[i], y[i + 8]);
+    for (int i = 0; i < H; ++i) unpack_f32x2(Y[i], y[i], y[i + H]);
 }
 
 }  // namespace fx
