@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-hwp", action="store_true", help="skip the step timing with a half-wave plate")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, precision-sweep and gradient measurements")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the fused P^T N^-1 P apply (profiling runs; not a bench line)")
     ap.add_argument("--ndet", type=int, default=None, help="override the detector count (profiling runs)")
@@ -274,6 +276,116 @@ def hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps: int):
             "workload": "same scan, ideal half-wave plate at 46 rpm"}
 
 
+def batched_c4(fx, dev, stream, steps: int):
+    """The batched configuration: 64 independent observations, lengths uniform in [2^18, 2^22],
+    8-128 detectors, nside 256/512 alternating (9.75 G samples), one launch per operator over the
+    whole ragged batch, per-observation PCG. The boresight of observation i is the slice starting
+    at 4096 i of one 2^22 + 2^18-sample scan (host generation of 141 M scan samples would take
+    minutes); the data are P of a random map per observation."""
+    import torch
+    shapes = synth.config4_shapes()
+    base = torch.from_numpy(synth.satellite_scan(max(ns for _, _, ns in shapes) + 64 * 4096))
+    qb = torch.cat([base[4096 * i: 4096 * i + ns] for i, (_, _, ns) in enumerate(shapes)]).to(dev)
+    qd = torch.cat([torch.from_numpy(synth.hex_focal_plane(nd)) for _, nd, _ in shapes]).to(dev)
+    nds, nss, nsides = [nd for _, nd, _ in shapes], [ns for _, _, ns in shapes], [n for n, _, _ in shapes]
+    S = sum(nd * ns for _, nd, ns in shapes)
+    taps = np.tile(synth.inverse_noise_taps(), (sum(nds), 1))
+    from paper_2603_19600_gb300 import _native as nat
+    with torch.cuda.stream(stream):
+        P = fx.Pointing(qb, qd, nds, nss, nsides, mode="cache_f32", stream=stream)
+        N = fx.Noise.banded(P, taps)
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 404)
+        m = torch.randn(P.npix_total, 3, generator=g, device=dev, dtype=torch.float64)
+        d = P.apply(m.float())
+        x = torch.randn(P.npix_total, 3, generator=g, device=dev, dtype=torch.float64)
+        fx.ptnp_apply(P, N, x, None, "f32", "f32")
+        nat.furax_profile_reset()
+        nat.furax_profile_enable(True)
+        for _ in range(3):
+            fx.ptnp_apply(P, N, x, None, "f32", "f32")
+        stream.synchronize()
+        nat.furax_profile_enable(False)
+        apply_ms, n = nat.furax_profile_read(0)
+        apply_ms /= max(n, 1)
+
+        def step():
+            P.refresh()
+            return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=0.0,
+                                  max_outer=1, true_residual=False, check_every=10)
+        step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+        P.close()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "64 observations, lengths uniform in [2^18, 2^22], 8-128 detectors, nside 256/512",
+            "samples": S, "observations": 64, "apply_ms": apply_ms, "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
+            "step_ms": ms, "value": S * CG_ITERS / (ms / 1e3) / 1e9, "unit": UNIT, "steps": steps}
+
+
+def precision_sweep(fx, dev, stream):
+    """4 co-pointed detectors (0/45/90/135 deg), 65,536 samples, white noise: maps from FP32 TOD
+    with FP32, compensated FP32 and FP64 per-pixel accumulation, relative error against the FP64
+    solve of the same data, at nside 256, 512 and 1024."""
+    import torch
+    out = {}
+    for nside in (256, 512, 1024):
+        obs, sky, noise, sigma2 = synth.config1(nside=nside)
+        with torch.cuda.stream(stream):
+            P64 = fx.Pointing.from_observations([obs], mode="cache_f64", device=dev, stream=stream)
+            N64 = fx.Noise.white(P64, sigma2)
+            d = P64.apply(torch.as_tensor(sky, device=dev)) + torch.as_tensor(noise.ravel(), device=dev)
+            d32 = d.float()
+            x64, v, _ = fx.mapmaker_cg(P64, N64, d32.double(), maxiter=30, tol=1e-12, precision="f64")
+            v = v.bool()
+            P32 = fx.Pointing.from_observations([obs], mode="cache_f32", device=dev, stream=stream)
+            N32 = fx.Noise.white(P32, sigma2)
+            row = {"valid_pixels": int(v.sum().item())}
+            for acc in ("f32", "f32_kahan", "f64"):
+                x, _, _ = fx.mapmaker_cg(P32, N32, d32, maxiter=30, tol=1e-8, precision="f32", acc=acc)
+                row[acc] = float(torch.linalg.norm(x[v] - x64[v]) / torch.linalg.norm(x64[v]))
+            P64.close(); P32.close()
+        out[str(nside)] = row
+    return {"workload": "config 1: 4 co-pointed detectors x 65536 samples, white noise, FP32 TOD",
+            "map_rel_error_vs_fp64": out}
+
+
+def gradient_c5(fx, dev, stream, reps: int = 3):
+    """The differentiable configuration: nside 256, 128 detectors x 2^20 samples, offsets
+    ~ N(0, 1 deg): chi^2 with d chi^2/d m and d chi^2/d delta per evaluation."""
+    import torch
+    nd, ns, nside = 128, 1 << 20, 256
+    g = synth.rng(5, 0)
+    qb = torch.from_numpy(synth.satellite_scan(ns)).to(dev)
+    qd = torch.from_numpy(synth.hex_focal_plane(nd)).to(dev)
+    delta = torch.from_numpy(np.radians(g.normal(0.0, 1.0, nd))).to(dev)
+    taps = np.tile(synth.inverse_noise_taps(), (nd, 1))
+    res = {"workload": "128 detectors x 2^20 samples, nside 256, per-detector angle offsets ~ N(0, 1 deg)"}
+    with torch.cuda.stream(stream):
+        P = fx.Pointing(qb, qd, [nd], [ns], [nside], psi_offset=delta, mode="cache_f64", stream=stream)
+        N = fx.Noise.banded(P, taps)
+        sky = torch.from_numpy(synth.gaussian_sky(nside, g)).to(dev)
+        d = P.apply(sky)
+        m = sky * 1.01
+        for prec, dd in (("f64", d), ("f32", d.float())):
+            fx.chi2_grad(P, N, dd, m, prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fx.chi2_grad(P, N, dd, m, prec)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[prec] = {"ms_per_evaluation": ms, "gsamples_per_s": nd * ns / (ms / 1e3) / 1e9}
+        P.close()
+    return res
+
+
 def _wl_name(wl):
     return (f"satellite scan, {wl['ndet']} detectors (hex focal plane, radius 5 deg) x {wl['nsamp']} samples, "
             f"HEALPix nside {wl['nside']}, 1/f + white noise, 64-tap banded N^-1, {CG_ITERS} PCG iterations")
@@ -441,6 +553,16 @@ def main():
     # ---------------- the same step with a half-wave plate (HWP-modulated pointing)
     if not args.no_hwp:
         out["hwp"] = hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps=max(1, min(args.steps, 3)))
+    # ---------------- the other configurations of the workload: batched, precision, gradients
+    if rank == 0 and world == 1 and not args.no_extra and not args.small:
+        for key, fn in (("precision_sweep", lambda: precision_sweep(fx, dev, stream)),
+                        ("gradient", lambda: gradient_c5(fx, dev, stream)),
+                        ("batched", lambda: batched_c4(fx, dev, stream, steps=1))):
+            try:   # secondary measurements: a failure is reported in its field, not in the headline
+                out[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                out[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+            torch.cuda.empty_cache()
     # ---------------- solve to a true residual of 1e-8 on the same workload: mixed vs plain FP64
     if rank == 0 and not args.no_cg1e8 and world == 1:
         out["cg_to_1e-8"] = cg_to_1e8(fx, dev, stream, wl, q_bore, q_det, d)
