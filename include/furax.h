@@ -80,6 +80,7 @@ typedef enum { FURAX_NOISE_WHITE = 0, FURAX_NOISE_BANDED = 1 } furax_noise_kind;
 
 typedef struct furax_pointing furax_pointing_t;
 typedef struct furax_noise furax_noise_t;
+typedef struct furax_templates furax_templates_t;
 
 /* A batch of independent observations (one map each). */
 typedef struct {
@@ -271,6 +272,44 @@ void furax_cg_default_opts(furax_cg_opts *opts);
 furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
                                double *x, uint8_t *valid, const furax_cg_opts *opts, furax_cg_result *res,
                                void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Template deprojection: the weighting-and-deprojection operator
+ *   F_T = W - W T (T^T W T)^-1 T^T W
+ * of the generalised least-squares estimator m = (P^T F_T P)^-1 P^T F_T d (Statement of Need;
+ * TemplateOperator, Table 3). W = N^-1 of a noise handle. T, per detector: the Legendre
+ * polynomials P_0 .. P_order (order <= 3) of the scaled time tau_t = 2t/(ns-1) - 1 over the
+ * detector's whole stream (tau = 0 when ns = 1). F_T acts on each detector separately.
+ * With P_0 among the templates, a constant I map is deprojected with the offsets: the I
+ * monopole of the observed pixels is not constrained by the data.
+ * ------------------------------------------------------------------------------------- */
+
+/* Build the per-detector Gram matrices G = T^T W T (FP64, on the device) and their inverses.
+ * p and n (same detectors and streams) are kept by reference and must outlive the handle.
+ * Synchronises `stream`. FURAX_EINVAL: order outside [0, 3] or mismatched handles.
+ * FURAX_EBADINPUT: a stream shorter than order + 1 samples, or a G that is not positive
+ * definite (the message names the detector). */
+furax_status furax_templates_create(const furax_pointing_t *p, const furax_noise_t *n, int32_t order, void *stream,
+                                    furax_templates_t **out);
+furax_status furax_templates_destroy(furax_templates_t *t);
+
+/* gram: device FP64 [sum ndet][order+1][order+1] <- T^T W T per detector. */
+furax_status furax_templates_gram(const furax_templates_t *t, double *gram, void *stream);
+
+/* out = F_T in over the whole TOD (device, [nsamp_total] of dtype; in and out must not alias). */
+furax_status furax_deproject_apply(const furax_templates_t *t, const void *in, void *out, int32_t dtype, void *stream);
+
+/* out = S P^T F_T P S^T x: the deprojected normal operator (precision and acc as for
+ * furax_ptnp_apply). x, out: device FP64 [npix_total][3]; valid: device uint8 or NULL. */
+furax_status furax_ptfp_apply(const furax_templates_t *t, const double *x, double *out, const uint8_t *valid,
+                              int32_t precision, int32_t acc, void *stream);
+
+/* furax_mapmaker_cg for the deprojected system (S P^T F_T P S^T) x = S P^T F_T d (same options,
+ * preconditioner, mask and result). amplitudes: device FP64 [sum ndet][order+1] receiving
+ * G^-1 (W T)^T (d - P x) of the solved map, or NULL. */
+furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void *d, int32_t d_t, double *x,
+                                         uint8_t *valid, const furax_cg_opts *opts, furax_cg_result *res,
+                                         double *amplitudes, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * chi^2 and its gradients (differentiability, "Summary"; "Research Impact Statement").

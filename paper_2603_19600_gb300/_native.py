@@ -74,6 +74,12 @@ _SIGS = {
     "furax_ptnp_apply_noalloc": [_V, _V, _V, _I32, _I64, _I32, _V, _I32, _V, _V, _V, _V],
     "furax_mapmaker_cg": [_V, _V, _V, _I32, _V, _V, ctypes.POINTER(CgOpts), ctypes.POINTER(CgResult), _V],
     "furax_chi2_grad": [_V, _V, _V, _I32, _V, _V, _V, _V, _I32, _V],
+    "furax_templates_create": [_V, _V, _I32, _V, ctypes.POINTER(_V)],
+    "furax_templates_destroy": [_V],
+    "furax_templates_gram": [_V, _V, _V],
+    "furax_deproject_apply": [_V, _V, _V, _I32, _V],
+    "furax_ptfp_apply": [_V, _V, _V, _V, _I32, _I32, _V],
+    "furax_mapmaker_cg_deproject": [_V, _V, _I32, _V, _V, ctypes.POINTER(CgOpts), ctypes.POINTER(CgResult), _V, _V],
 }
 
 _lock = threading.Lock()
@@ -294,6 +300,46 @@ def furax_mapmaker_cg(hp, hn, d, x, valid=None, opts: CgOpts | None = None, hist
     rc = _call("furax_mapmaker_cg", hp, hn, _ptr(d, None, None, "d"), _dt(d), _ptr(x, torch.float64, None, "x"),
                _ptr(valid, torch.uint8, None, "valid"), ctypes.byref(o), ctypes.byref(res), _stream(stream),
                ok=(FURAX_OK, FURAX_ENOTCONVERGED))
+    return rc, res, [hist[i] for i in range(res.hist_written)]
+
+
+def furax_templates_create(hp, hn, order, stream=None) -> int:
+    h = _V()
+    _call("furax_templates_create", hp, hn, int(order), _stream(stream), ctypes.byref(h))
+    return h.value
+
+
+def furax_templates_destroy(h) -> None:
+    if h:
+        _call("furax_templates_destroy", h)
+
+
+def furax_templates_gram(h, gram, stream=None) -> None:
+    _call("furax_templates_gram", h, _ptr(gram, torch.float64, None, "gram"), _stream(stream))
+
+
+def furax_deproject_apply(h, x, out, stream=None) -> None:
+    if x.dtype != out.dtype:
+        raise ValueError("in and out must have the same dtype")
+    _call("furax_deproject_apply", h, _ptr(x, None, None, "in"), _ptr(out, None, x.numel(), "out"), _dt(x),
+          _stream(stream))
+
+
+def furax_ptfp_apply(ht, x, out, valid=None, precision=FURAX_F32, acc=FURAX_ACC_F32, stream=None) -> None:
+    _call("furax_ptfp_apply", ht, _ptr(x, torch.float64, None, "x"), _ptr(out, torch.float64, x.numel(), "out"),
+          _ptr(valid, torch.uint8, None, "valid"), precision, acc, _stream(stream))
+
+
+def furax_mapmaker_cg_deproject(ht, d, x, valid=None, opts: CgOpts | None = None, hist_len=0, amplitudes=None,
+                                stream=None):
+    o = opts if opts is not None else default_cg_opts()
+    res = CgResult()
+    hist = (ctypes.c_double * max(hist_len, 1))()
+    res.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist_len > 0 else None
+    res.hist_len = hist_len
+    rc = _call("furax_mapmaker_cg_deproject", ht, _ptr(d, None, None, "d"), _dt(d), _ptr(x, torch.float64, None, "x"),
+               _ptr(valid, torch.uint8, None, "valid"), ctypes.byref(o), ctypes.byref(res),
+               _ptr(amplitudes, torch.float64, None, "amplitudes"), _stream(stream), ok=(FURAX_OK, FURAX_ENOTCONVERGED))
     return rc, res, [hist[i] for i in range(res.hist_written)]
 
 

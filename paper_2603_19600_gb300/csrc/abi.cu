@@ -622,6 +622,72 @@ furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n
     return mapmaker_cg(p, n, d, d_t, x, valid, o, res, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------- templates
+furax_status furax_templates_create(const furax_pointing_t *p, const furax_noise_t *n, int32_t order, void *stream,
+                                    furax_templates_t **out)
+{
+    REQUIRE(out, "out must be a host pointer");
+    *out = nullptr;
+    furax_status rc = check_pair(p, n);
+    if (rc) return rc;
+    REQUIRE(n->nsamp_total == p->nsamp_total, "noise streams hold %lld samples, pointing %lld",
+            (long long)n->nsamp_total, (long long)p->nsamp_total);
+    REQUIRE(order >= 0 && order <= 3, "template order %d outside [0, 3]", order);
+    return templates_create(p, n, order, (cudaStream_t)stream, out);
+}
+
+furax_status furax_templates_destroy(furax_templates_t *t)
+{
+    templates_destroy(t);
+    return FURAX_OK;
+}
+
+furax_status furax_templates_gram(const furax_templates_t *t, double *gram, void *stream)
+{
+    REQUIRE(t, "templates handle is NULL");
+    REQUIRE(gram, "gram must be a device pointer");
+    return tpl_gram_out(t, gram, (cudaStream_t)stream);
+}
+
+furax_status furax_deproject_apply(const furax_templates_t *t, const void *in, void *out, int32_t dtype, void *stream)
+{
+    REQUIRE(t, "templates handle is NULL");
+    REQUIRE(in && out, "in and out must be device pointers");
+    REQUIRE(in != out, "in and out must not alias");
+    REQUIRE(valid_dtype(dtype), "unknown dtype %d", dtype);
+    return deproject_apply(t, in, out, dtype, (cudaStream_t)stream);
+}
+
+furax_status furax_ptfp_apply(const furax_templates_t *t, const double *x, double *out, const uint8_t *valid,
+                              int32_t precision, int32_t acc, void *stream)
+{
+    REQUIRE(t, "templates handle is NULL");
+    REQUIRE(x && out, "x and out must be device pointers");
+    REQUIRE(x != out, "x and out must not alias");
+    REQUIRE(valid_dtype(precision) || precision == FURAX_PREC_F32X2, "unknown precision %d", precision);
+    REQUIRE(valid_acc(acc), "unknown accumulation mode %d", acc);
+    return ptnp_apply(t->p, t->n, x, out, valid, precision, acc, (cudaStream_t)stream, t);
+}
+
+furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void *d, int32_t d_t, double *x,
+                                         uint8_t *valid, const furax_cg_opts *o, furax_cg_result *res,
+                                         double *amplitudes, void *stream)
+{
+    REQUIRE(t, "templates handle is NULL");
+    REQUIRE(d && x, "d and x must be device pointers");
+    REQUIRE(o && res, "opts and result must be host pointers");
+    REQUIRE(valid_dtype(d_t), "unknown dtype %d", d_t);
+    REQUIRE(o->maxiter >= 0 && o->maxiter <= 1000000, "maxiter out of range");
+    REQUIRE(o->tol >= 0.0, "tol must be >= 0");
+    REQUIRE(valid_dtype(o->precision), "unknown precision %d", o->precision);
+    REQUIRE(valid_acc(o->acc), "unknown accumulation mode %d", o->acc);
+    REQUIRE(o->precision == FURAX_F64 || (o->inner_tol >= 0.0 && o->inner_tol < 1.0 && o->max_outer >= 1),
+            "mixed precision needs 0 <= inner_tol < 1 and max_outer >= 1");
+    REQUIRE(o->check_every >= 1, "check_every must be >= 1");
+    REQUIRE(!res->hist || res->hist_len >= 0, "hist_len must be >= 0");
+    return mapmaker_cg(t->p, t->n, d, d_t, x, valid, o, res, (cudaStream_t)stream, t, amplitudes);
+}
+
 furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
                              const double *m, double *chi2, double *grad_map, double *grad_psi, int32_t precision,
                              void *stream)

@@ -64,6 +64,15 @@ struct NoiseView {
     const double *diag;     // diagonal of N^-1 per detector [ndet] (FP64)
 };
 
+// Template deprojection (per-detector Legendre templates, W = N^-1).
+struct TplView {
+    int32_t order;          // highest Legendre degree K (<= 3)
+    int32_t halo;           // band half-width of W (0 for white noise)
+    const double2 *mom;     // [ndet] (mu0, mu2): zeroth and second moments of the band
+    const double *ginv;     // [ndet][4][4] (T^T W T)^-1, zero beyond K
+    const double *b;        // [ndet][4] template amplitudes of the last solve
+};
+
 // Status helpers (thread-local message).
 furax_status set_error(furax_status code, const char *fmt, ...);
 furax_status check_cuda(cudaError_t e, const char *what);
@@ -138,6 +147,21 @@ struct furax_pointing {
     }
 };
 
+struct furax_templates {
+    const furax_pointing *p = nullptr;   // layout and pointing (caller-owned, outlives the handle)
+    const furax_noise *n = nullptr;      // W = N^-1 (caller-owned, outlives the handle)
+    int32_t order = 0;
+    int32_t halo = 0;
+    int64_t ndet = 0;
+    double2 *mom = nullptr;
+    double *gram = nullptr;              // [ndet][4][4] T^T W T
+    double *ginv = nullptr;              // [ndet][4][4]
+    double *a = nullptr;                 // [ndet][4] projections (kept zero between uses)
+    double *b = nullptr;                 // [ndet][4]
+    unsigned long long *bad = nullptr;   // setup status (1 + first detector with a singular Gram matrix)
+    fx::TplView view() const { return fx::TplView{order, halo, mom, ginv, b}; }
+};
+
 struct furax_noise {
     int32_t kind = 0;
     int32_t ntaps = 0;
@@ -209,8 +233,27 @@ furax_status launch_finalize_acc(const furax_pointing *p, int acc, const float4 
 furax_status launch_mask_copy(const furax_pointing *p, const double *x, const uint8_t *valid, double *out,
                               cudaStream_t st);
 furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const double *x, double *out,
-                        const uint8_t *valid, int precision, int acc, cudaStream_t st);
+                        const uint8_t *valid, int precision, int acc, cudaStream_t st,
+                        const furax_templates *tp = nullptr);
 furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *x,
-                         uint8_t *valid, const furax_cg_opts *o, furax_cg_result *res, cudaStream_t st);
+                         uint8_t *valid, const furax_cg_opts *o, furax_cg_result *res, cudaStream_t st,
+                         const furax_templates *tp = nullptr, double *amplitudes = nullptr);
+
+// ---- template deprojection (templates.cu)
+furax_status templates_create(const furax_pointing *p, const furax_noise *n, int order, cudaStream_t st,
+                              furax_templates **out);
+void templates_destroy(furax_templates *tp);
+// acc -= P^T (W T) G^-1 (W T)^T P x; FP32 (x32, acc mode) or FP64 (x64, acc64) arithmetic.
+furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, const float4 *x32, const double *x64,
+                            float4 *hi, float4 *lo, double *acc64, cudaStream_t st);
+// acc64 -= P^T (W T) G^-1 (W T)^T d (FP64 arithmetic).
+furax_status launch_tpl_rhs(const furax_templates *tp, const void *d, int d_t, double *acc64, cudaStream_t st);
+// amp [ndet][K+1] = G^-1 (W T)^T (d - P m) (m: FP64 map, zero on masked pixels).
+furax_status tpl_amplitudes(const furax_templates *tp, const void *d, int d_t, const double *m, double *amp,
+                            cudaStream_t st);
+// out [ndet][K+1][K+1] = T^T W T.
+furax_status tpl_gram_out(const furax_templates *tp, double *out, cudaStream_t st);
+// out = F_T in for a TOD (in != out).
+furax_status deproject_apply(const furax_templates *tp, const void *in, void *out, int dtype, cudaStream_t st);
 
 }  // namespace fx

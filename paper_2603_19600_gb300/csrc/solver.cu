@@ -42,6 +42,7 @@ struct CgWs {
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0, graph_prec = -1, graph_acc = -1;
     const void *graph_noise = nullptr;
+    const void *graph_tpl = nullptr;
     const double *graph_x = nullptr;
     double graph_tol2 = -1.0;
     bool graph_prof = false;
@@ -155,7 +156,7 @@ furax_status launch_mask_copy(const furax_pointing *p, const double *x, const ui
 
 // out = S P^T N^-1 P S^T x
 furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const double *x, double *out,
-                        const uint8_t *valid, int precision, int acc, cudaStream_t st)
+                        const uint8_t *valid, int precision, int acc, cudaStream_t st, const furax_templates *tp)
 {
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     const int64_t np = p->npix_total;
@@ -174,6 +175,8 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
         } else {
             if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, xin, nullptr, 0, pm->ws_acc64, st); }))) return rc;
         }
+        if (tp && (rc = launch_tpl_map(tp, FURAX_F64, FURAX_ACC_F64, nullptr, xin, nullptr, nullptr, pm->ws_acc64, st)))
+            return rc;
         return launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, pm->ws_acc64, valid, out, st);
     }
     if ((rc = ensure_ws(pm, (void **)&pm->ws_map32, sizeof(float4) * np))) return rc;
@@ -193,6 +196,7 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
     }
     if ((rc = launch_pack_x32(p, x, valid, pm->ws_map32, hi, lo, st))) return rc;
     if ((rc = timed(0, st, [&] { return launch_fused_f32(p, n, pm->ws_map32, acc, hi, lo, a64, st); }))) return rc;
+    if (tp && (rc = launch_tpl_map(tp, FURAX_F32, acc, pm->ws_map32, nullptr, hi, lo, a64, st))) return rc;
     return launch_finalize_acc(p, acc, hi, lo, a64, valid, out, st);
 }
 
@@ -486,6 +490,7 @@ struct Body {
     double tol2;
     double *x;
     unsigned pg;   // pixel-tile grid
+    const furax_templates *tp;   // template deprojection, or nullptr
 };
 
 // One PCG iteration: q = A p, alpha, x/r/z update, beta, new direction (+ accumulator reset).
@@ -503,6 +508,9 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
         if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st))) return rc;
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    if (b.tp && (rc = launch_tpl_map(b.tp, b.precision == FURAX_F64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi,
+                                     w->lo, w->acc64, st)))
+        return rc;
     cg_q_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
     cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc);
     cg_update_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
@@ -530,7 +538,7 @@ static furax_status body_prologue(const Body &b, cudaStream_t st)
     return check_launch("PCG prologue");
 }
 
-static int64_t graph_nodes_per_iter(const Body &) { return 6; }
+static int64_t graph_nodes_per_iter(const Body &b) { return b.tp ? 9 : 6; }
 
 // Run PCG from b (in w->bfull or a given rhs) into x. Returns iterations used (max over obs).
 static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_graph, int check_every,
@@ -556,7 +564,7 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
             const bool prof = prof_on();
             const bool rebuild = !w->graph || w->graph_iters != n || w->graph_prec != b.precision ||
                                  w->graph_acc != b.acc || w->graph_noise != (const void *)b.n || w->graph_x != b.x ||
-                                 w->graph_tol2 != b.tol2 || w->graph_prof != prof;
+                                 w->graph_tol2 != b.tol2 || w->graph_prof != prof || w->graph_tpl != (const void *)b.tp;
             if (rebuild) {
                 if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
                 while (prof && (int)w->ev.size() < 2 * n) {
@@ -579,7 +587,7 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
                 cudaGraphDestroy(g);
                 if ((rc = check_cuda(e, "graph instantiate"))) return rc;
                 w->graph_iters = n; w->graph_prec = b.precision; w->graph_acc = b.acc; w->graph_noise = b.n;
-                w->graph_x = b.x; w->graph_tol2 = b.tol2; w->graph_prof = prof;
+                w->graph_x = b.x; w->graph_tol2 = b.tol2; w->graph_prof = prof; w->graph_tpl = b.tp;
             }
             if ((rc = check_cuda(cudaGraphLaunch(w->graph, st), "graph launch"))) return rc;
             count_launches(graph_nodes_per_iter(b) * n);
@@ -634,6 +642,8 @@ static furax_status true_residual(const Body &b, const double *x, double *rtrue,
     } else {
         if ((rc = timed(2, st, [&] { return launch_fused_df(p, b.n, x, nullptr, 0, w->acc64, st); }))) return rc;
     }
+    if (b.tp && (rc = launch_tpl_map(b.tp, FURAX_F64, FURAX_ACC_F64, nullptr, x, nullptr, nullptr, w->acc64, st)))
+        return rc;
     residual_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->bfull, w->acc64, w->valid, rtrue, w->partial);
     double *norms = w->q;   // scratch [n_obs][2] (q is free here)
     obs_norms_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, norms);
@@ -651,7 +661,8 @@ static furax_status true_residual(const Body &b, const double *x, double *rtrue,
 }
 
 furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *x,
-                         uint8_t *valid_out, const furax_cg_opts *o, furax_cg_result *res, cudaStream_t st)
+                         uint8_t *valid_out, const furax_cg_opts *o, furax_cg_result *res, cudaStream_t st,
+                         const furax_templates *tp, double *amplitudes)
 {
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     CgWs *w = nullptr;
@@ -669,11 +680,12 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     } else {
         if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, nullptr, d, d_t, w->acc64, st); }))) return rc;
     }
+    if (tp && (rc = launch_tpl_rhs(tp, d, d_t, w->acc64, st))) return rc;
     if ((rc = launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, w->acc64, w->valid, w->bfull, st))) return rc;
     if (valid_out && (rc = check_cuda(cudaMemcpyAsync(valid_out, w->valid, np, cudaMemcpyDeviceToDevice, st), "copy mask")))
         return rc;
 
-    Body b{p, n, w, o->precision, o->acc, o->tol * o->tol, x, pg};
+    Body b{p, n, w, o->precision, o->acc, o->tol * o->tol, x, pg, tp};
     int total_iters = 0, outer = 0;
     bool converged = false;
     double rel = 0.0, true_rel = 0.0;
@@ -732,6 +744,7 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
             if (it == 0) break;
         }
     }
+    if (tp && amplitudes && (rc = tpl_amplitudes(tp, d, d_t, x, amplitudes, st))) return rc;
     res->iters = total_iters;
     res->outer = outer;
     res->rel_res = rel;

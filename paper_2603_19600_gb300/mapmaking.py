@@ -162,6 +162,49 @@ class Noise:
         return out
 
 
+class Templates:
+    """Template deprojection F_T = W - W T (T^T W T)^-1 T^T W with W = N^-1 and, per detector, the
+    Legendre polynomials P_0..P_order (order <= 3) of the scaled time 2t/(ns-1) - 1."""
+
+    def __init__(self, pointing: Pointing, noise: Noise, order: int, stream=None):
+        self.pointing, self.noise, self.order = pointing, noise, int(order)
+        self.handle = None
+        self.handle = nat.furax_templates_create(pointing.handle, noise.handle, self.order, stream)
+
+    def close(self):
+        if self.handle:
+            nat.furax_templates_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gram(self):
+        """T^T W T per detector: float64 [ndet_total][order+1][order+1]."""
+        k = self.order + 1
+        g = torch.empty(self.pointing.ndet_total, k, k, dtype=torch.float64, device=self.pointing.device)
+        nat.furax_templates_gram(self.handle, g)
+        return g
+
+    def deproject(self, tod, out=None):
+        """F_T tod over the whole TOD (float32 or float64 [nsamp_total])."""
+        out = torch.empty_like(tod) if out is None else out
+        nat.furax_deproject_apply(self.handle, tod.contiguous(), out)
+        return out
+
+
+def ptfp_apply(T: Templates, x, valid=None, precision="f32", acc="f32", out=None):
+    """out = S P^T F_T P S^T x (x float64 [npix_total][3])."""
+    if out is None:
+        out = torch.empty_like(x)
+    v = None if valid is None else valid.to(torch.uint8).contiguous()
+    nat.furax_ptfp_apply(T.handle, x.contiguous(), out, v, _PREC[precision], _ACC[acc])
+    return out
+
+
 def blockdiag_precond(P: Pointing, N: Noise, rcond_min=1e-3):
     inv = torch.empty(P.npix_total, 6, dtype=torch.float64, device=P.device)
     valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
@@ -204,8 +247,10 @@ class SolveInfo:
 
 def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64", acc="f32", inner_tol=1e-5,
                 max_outer=8, use_graph=True, check_every=10, rcond_min=1e-3, binned_only=False, hist_len=None,
-                out=None, true_residual=True):
-    """Solve the map-making normal equations per observation; returns (map, valid mask, SolveInfo)."""
+                out=None, true_residual=True, templates: "Templates | None" = None, amplitudes=None):
+    """Solve the map-making normal equations per observation; returns (map, valid mask, SolveInfo).
+    With ``templates`` the system is the deprojected one (P^T F_T P) x = P^T F_T d; ``amplitudes``
+    (float64 [ndet_total][order+1], optional) then receives the template amplitudes of the map."""
     o = nat.default_cg_opts()
     o.maxiter, o.tol, o.precision, o.acc = int(maxiter), float(tol), _PREC[precision], _ACC[acc]
     o.inner_tol, o.max_outer, o.use_graph = float(inner_tol), int(max_outer), int(bool(use_graph))
@@ -213,8 +258,13 @@ def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64",
     o.true_residual = int(bool(true_residual))
     x = out if out is not None else torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device)
     valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
-    rc, res, hist = nat.furax_mapmaker_cg(P.handle, N.handle, d.contiguous(), x, valid, o,
-                                          hist_len if hist_len is not None else maxiter + 1)
+    hl = hist_len if hist_len is not None else maxiter + 1
+    if templates is not None:
+        if templates.pointing is not P or templates.noise is not N:
+            raise ValueError("templates were built for another pointing or noise")
+        rc, res, hist = nat.furax_mapmaker_cg_deproject(templates.handle, d.contiguous(), x, valid, o, hl, amplitudes)
+    else:
+        rc, res, hist = nat.furax_mapmaker_cg(P.handle, N.handle, d.contiguous(), x, valid, o, hl)
     return x, valid.bool(), SolveInfo(rc, res.iters, res.outer, res.rel_res, res.true_rel_res, res.n_valid, hist)
 
 
