@@ -108,11 +108,14 @@ __device__ __forceinline__ TileSpan tile_span(const Tile &tl, const ObsInfo &ob,
     return sp;
 }
 
-template <int ACC, bool BANDED>
+// With TPL the consumers also accumulate T^T z per detector into tpl_a[det][4] (z = N^-1 P x
+// of the tile's samples, T = Legendre P_0..P_3 of tau_t = 2t/(ns-1) - 1): the projection of the
+// template-deprojected operator, which then needs no pass of its own.
+template <int ACC, bool BANDED, bool TPL>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     fused_tma_kernel(const Tile *__restrict__ tiles, int64_t n_tiles, PointingView pv, NoiseView nv,
                      const float4 *__restrict__ x32, float4 *__restrict__ acc_hi, float4 *__restrict__ acc_lo,
-                     double *__restrict__ acc64, unsigned *__restrict__ err)
+                     double *__restrict__ acc64, unsigned *__restrict__ err, double *__restrict__ tpl_a)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     TmaSmem &S = *reinterpret_cast<TmaSmem *>(tsm);
@@ -224,6 +227,28 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         // Every consumer has read its stencil inputs: y overwrites the stage in place (core
         // sample u at slot spos(u)), which is released to the gathers after the scatter.
         if (!consumers_all(ok)) break;
+        if constexpr (TPL) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            if (base < tl.len) {
+                const float h = ob.nsamp > 1 ? 2.f / (float)(ob.nsamp - 1) : 0.f;
+#pragma unroll
+                for (int i = 0; i < kConsOut; ++i) {
+                    if (base + i >= tl.len) break;
+                    const float tau = ob.nsamp > 1 ? (float)(tl.t0 + base + i) * h - 1.f : 0.f;
+                    a[0] += y[i];
+                    a[1] += tau * y[i];
+                    a[2] += (1.5f * tau * tau - 0.5f) * y[i];
+                    a[3] += tau * (2.5f * tau * tau - 1.5f) * y[i];
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a[l] += __shfl_down_sync(0xffffffffu, a[l], o);
+            if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) red_add_f64(tpl_a + 4 * gdet + l, (double)a[l]);
+        }
         float *ys = S.xs[q];
 #pragma unroll
         for (int i = 0; i < kConsOut; ++i)
@@ -257,40 +282,51 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 }
 
-template <int ACC, bool BANDED>
+template <int ACC, bool BANDED, bool TPL>
 static furax_status run_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, float4 *hi, float4 *lo,
-                            double *a64, cudaStream_t st)
+                            double *a64, double *tpl_a, cudaStream_t st)
 {
     const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
-    return launch_dyn(fused_tma_kernel<ACC, BANDED>, g, kTmaThreads, kTmaSmem, st, p->d_tiles, p->n_tiles, p->view(),
-                      n->view(), x32, hi, lo, a64, p->d_err);
+    return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL>, g, kTmaThreads, kTmaSmem, st, p->d_tiles, p->n_tiles,
+                      p->view(), n->view(), x32, hi, lo, a64, p->d_err, tpl_a);
 }
 
-template <bool BANDED>
+template <bool BANDED, bool TPL>
 static furax_status dispatch_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                                 float4 *lo, double *a64, cudaStream_t st)
+                                 float4 *lo, double *a64, double *tpl_a, cudaStream_t st)
 {
-    if (acc == FURAX_ACC_F32) return run_tma<FURAX_ACC_F32, BANDED>(p, n, x32, hi, lo, a64, st);
-    if (acc == FURAX_ACC_F32_KAHAN) return run_tma<FURAX_ACC_F32_KAHAN, BANDED>(p, n, x32, hi, lo, a64, st);
-    return run_tma<FURAX_ACC_F64, BANDED>(p, n, x32, hi, lo, a64, st);
+    if (acc == FURAX_ACC_F32) return run_tma<FURAX_ACC_F32, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
+    if (acc == FURAX_ACC_F32_KAHAN) return run_tma<FURAX_ACC_F32_KAHAN, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
+    return run_tma<FURAX_ACC_F64, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
 }
 
 furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                              float4 *lo, double *a64, cudaStream_t st)
+                              float4 *lo, double *a64, cudaStream_t st, double *tpl_a)
 {
-    return n->kind == FURAX_NOISE_BANDED ? dispatch_tma<true>(p, n, x32, acc, hi, lo, a64, st)
-                                         : dispatch_tma<false>(p, n, x32, acc, hi, lo, a64, st);
+    const bool b = n->kind == FURAX_NOISE_BANDED;
+    if (tpl_a)
+        return b ? dispatch_tma<true, true>(p, n, x32, acc, hi, lo, a64, tpl_a, st)
+                 : dispatch_tma<false, true>(p, n, x32, acc, hi, lo, a64, tpl_a, st);
+    return b ? dispatch_tma<true, false>(p, n, x32, acc, hi, lo, a64, nullptr, st)
+             : dispatch_tma<false, false>(p, n, x32, acc, hi, lo, a64, nullptr, st);
+}
+
+template <bool BANDED, bool TPL>
+static furax_status prepare_tma_band()
+{
+    furax_status rc = FURAX_OK;
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, BANDED, TPL>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, BANDED, TPL>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, BANDED, TPL>, kTmaSmem);
+    return rc;
 }
 
 furax_status prepare_fused_tma()
 {
-    furax_status rc = FURAX_OK;
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, true>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, true>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, true>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, false>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, false>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, false>, kTmaSmem);
+    furax_status rc = prepare_tma_band<true, false>();
+    if (!rc) rc = prepare_tma_band<false, false>();
+    if (!rc) rc = prepare_tma_band<true, true>();
+    if (!rc) rc = prepare_tma_band<false, true>();
     return rc;
 }
 

@@ -213,8 +213,12 @@ furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, con
 
 // ---- launchers (fused.cu)
 // acc_* workspaces must be zeroed by the caller; x32 is the padded FP32 copy of the (masked) input.
+// With tpl_a (cached FP32 pointing only: see fused_f32_projects_templates), the kernel also adds
+// the template projection T^T N^-1 P x per detector to tpl_a[det][4].
 furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
-                              float4 *acc_hi, float4 *acc_lo, double *acc64, cudaStream_t st);
+                              float4 *acc_hi, float4 *acc_lo, double *acc64, cudaStream_t st,
+                              double *tpl_a = nullptr);
+bool fused_f32_projects_templates(const furax_pointing *p);
 furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, const double *x, double *acc64,
                               cudaStream_t st);
 // FP64-accurate operator on FP32 units (double-FP32 band product): acc64 += P^T N^-1 P x, or
@@ -244,8 +248,12 @@ furax_status templates_create(const furax_pointing *p, const furax_noise *n, int
                               furax_templates **out);
 void templates_destroy(furax_templates *tp);
 // acc -= P^T (W T) G^-1 (W T)^T P x; FP32 (x32, acc mode) or FP64 (x64, acc64) arithmetic.
+// projected: the projection is already in tp->a (accumulated by the fused FP32 kernel).
 furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, const float4 *x32, const double *x64,
-                            float4 *hi, float4 *lo, double *acc64, cudaStream_t st);
+                            float4 *hi, float4 *lo, double *acc64, cudaStream_t st, bool projected = false);
+// The tp->a the fused FP32 operator should accumulate into, or nullptr (no templates, or a
+// pointing mode whose FP32 kernel does not project).
+double *tpl_fused_target(const furax_templates *tp, const furax_pointing *p);
 // acc64 -= P^T (W T) G^-1 (W T)^T d (FP64 arithmetic).
 furax_status launch_tpl_rhs(const furax_templates *tp, const void *d, int d_t, double *acc64, cudaStream_t st);
 // amp [ndet][K+1] = G^-1 (W T)^T (d - P m) (m: FP64 map, zero on masked pixels).

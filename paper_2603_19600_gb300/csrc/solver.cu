@@ -195,8 +195,11 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
         }
     }
     if ((rc = launch_pack_x32(p, x, valid, pm->ws_map32, hi, lo, st))) return rc;
-    if ((rc = timed(0, st, [&] { return launch_fused_f32(p, n, pm->ws_map32, acc, hi, lo, a64, st); }))) return rc;
-    if (tp && (rc = launch_tpl_map(tp, FURAX_F32, acc, pm->ws_map32, nullptr, hi, lo, a64, st))) return rc;
+    double *tpl_a = tpl_fused_target(tp, p);
+    if ((rc = timed(0, st, [&] { return launch_fused_f32(p, n, pm->ws_map32, acc, hi, lo, a64, st, tpl_a); })))
+        return rc;
+    if (tp && (rc = launch_tpl_map(tp, FURAX_F32, acc, pm->ws_map32, nullptr, hi, lo, a64, st, tpl_a != nullptr)))
+        return rc;
     return launch_finalize_acc(p, acc, hi, lo, a64, valid, out, st);
 }
 
@@ -505,12 +508,16 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
         if ((rc = launch_fused_f64(p, b.n, w->p, w->acc64, st))) return rc;
         acc = FURAX_ACC_F64;
     } else {
-        if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st))) return rc;
+        if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st, tpl_fused_target(b.tp, p))))
+            return rc;
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
-    if (b.tp && (rc = launch_tpl_map(b.tp, b.precision == FURAX_F64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi,
-                                     w->lo, w->acc64, st)))
-        return rc;
+    if (b.tp) {
+        const bool f64 = b.precision == FURAX_F64;
+        if ((rc = launch_tpl_map(b.tp, f64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi, w->lo, w->acc64, st,
+                                 !f64 && tpl_fused_target(b.tp, p) != nullptr)))
+            return rc;
+    }
     cg_q_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
     cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc);
     cg_update_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
@@ -538,7 +545,11 @@ static furax_status body_prologue(const Body &b, cudaStream_t st)
     return check_launch("PCG prologue");
 }
 
-static int64_t graph_nodes_per_iter(const Body &b) { return b.tp ? 9 : 6; }
+static int64_t graph_nodes_per_iter(const Body &b)
+{
+    if (!b.tp) return 6;
+    return b.precision != FURAX_F64 && tpl_fused_target(b.tp, b.p) ? 8 : 9;
+}
 
 // Run PCG from b (in w->bfull or a given rhs) into x. Returns iterations used (max over obs).
 static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_graph, int check_every,

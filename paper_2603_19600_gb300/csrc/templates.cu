@@ -355,12 +355,17 @@ static void solve(const furax_templates *tp, cudaStream_t st)
     tpl_solve_kernel<<<det_grid(tp->ndet), 128, 0, st>>>(tp->ndet, tp->ginv, tp->a, tp->b);
 }
 
+double *tpl_fused_target(const furax_templates *tp, const furax_pointing *p)
+{
+    return tp && fused_f32_projects_templates(p) ? tp->a : nullptr;
+}
+
 furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, const float4 *x32, const double *x64,
-                            float4 *hi, float4 *lo, double *acc64, cudaStream_t st)
+                            float4 *hi, float4 *lo, double *acc64, cudaStream_t st, bool projected)
 {
     if (tp->p->n_tiles == 0) return FURAX_OK;
     if (precision == FURAX_F32) {
-        project_mode<float, float4, false, float>(tp, x32, nullptr, st);
+        if (!projected) project_mode<float, float4, false, float>(tp, x32, nullptr, st);
         solve(tp, st);
         if (acc == FURAX_ACC_F32) scatter_mode<float, FURAX_ACC_F32>(tp, hi, lo, acc64, st);
         else if (acc == FURAX_ACC_F32_KAHAN) scatter_mode<float, FURAX_ACC_F32_KAHAN>(tp, hi, lo, acc64, st);
@@ -370,7 +375,7 @@ furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, c
         solve(tp, st);
         scatter_mode<double, FURAX_ACC_F64>(tp, hi, lo, acc64, st);
     }
-    count_launches(3);
+    count_launches(projected && precision == FURAX_F32 ? 2 : 3);
     return check_launch("template deprojection (map)");
 }
 
