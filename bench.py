@@ -325,7 +325,7 @@ def deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps: int, orde
             "apply_gsamples_per_s_deprojected": S / (apply_ms["deprojected"] / 1e3) / 1e9}
 
 
-def batched_c4(fx, dev, stream, steps: int):
+def batched_c4(fx, dev, stream, steps: int, joint: bool = False):
     """The batched configuration: 64 independent observations, lengths uniform in [2^18, 2^22],
     8-128 detectors, nside 256/512 alternating (9.75 G samples), one launch per operator over the
     whole ragged batch, per-observation PCG. The boresight of observation i is the slice starting
@@ -341,7 +341,9 @@ def batched_c4(fx, dev, stream, steps: int):
     taps = np.tile(synth.inverse_noise_taps(), (sum(nds), 1))
     from paper_2603_19600_gb300 import _native as nat
     with torch.cuda.stream(stream):
-        P = fx.Pointing(qb, qd, nds, nss, nsides, mode="cache_f32", stream=stream)
+        # joint: all observations of one nside solved into one map (two maps), else one map each
+        P = fx.Pointing(qb, qd, nds, nss, nsides, mode="cache_f32", stream=stream,
+                        map_id=nsides if joint else None)
         N = fx.Noise.banded(P, taps)
         g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 404)
         m = torch.randn(P.npix_total, 3, generator=g, device=dev, dtype=torch.float64)
@@ -371,8 +373,9 @@ def batched_c4(fx, dev, stream, steps: int):
         stream.synchronize()
         P.close()
     ms = e0.elapsed_time(e1) / steps
-    return {"workload": "64 observations, lengths uniform in [2^18, 2^22], 8-128 detectors, nside 256/512",
-            "samples": S, "observations": 64, "apply_ms": apply_ms, "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
+    return {"workload": "64 observations, lengths uniform in [2^18, 2^22], 8-128 detectors, nside 256/512"
+                        + (", one joint map per nside" if joint else ", one map per observation"),
+            "samples": S, "observations": 64, "maps": 2 if joint else 64, "apply_ms": apply_ms, "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
             "step_ms": ms, "value": S * CG_ITERS / (ms / 1e3) / 1e9, "unit": UNIT, "steps": steps}
 
 
@@ -613,7 +616,8 @@ def main():
                                                               steps=max(1, min(args.steps, 3)))),
                         ("precision_sweep", lambda: precision_sweep(fx, dev, stream)),
                         ("gradient", lambda: gradient_c5(fx, dev, stream)),
-                        ("batched", lambda: batched_c4(fx, dev, stream, steps=1))):
+                        ("batched", lambda: batched_c4(fx, dev, stream, steps=1)),
+                        ("batched_joint", lambda: batched_c4(fx, dev, stream, steps=1, joint=True))):
             try:   # secondary measurements: a failure is reported in its field, not in the headline
                 out[key] = fn()
             except Exception as e:  # noqa: BLE001

@@ -82,7 +82,7 @@ typedef struct furax_pointing furax_pointing_t;
 typedef struct furax_noise furax_noise_t;
 typedef struct furax_templates furax_templates_t;
 
-/* A batch of independent observations (one map each). */
+/* A batch of observations: each with its own map, or sharing maps by map_id. */
 typedef struct {
     int32_t n_obs;            /* >= 1 */
     const int32_t *ndet;      /* host [n_obs], each >= 1 */
@@ -96,6 +96,12 @@ typedef struct {
                                  With a plate (HWPOperator, Table 3) the weights become
                                  (1, cos(4w - 2psi), sin(4w - 2psi)); pixels do not change. Read once
                                  at creation (kept as cos 4w, sin 4w). */
+    const int32_t *map_id;    /* host [n_obs] or NULL (one map per observation). Observations with
+                                 equal map_id share one map and are solved jointly ("Algebraic
+                                 reductions": P^T N^-1 P = sum_i P_i^T N_i^-1 P_i over the
+                                 observations i of the map); they must have equal nside. Maps are
+                                 laid out in order of the first observation of each, and every
+                                 map-sized array ([npix_total][...]) follows that layout. */
 } furax_obs_desc;
 
 /* ---------------------------------------------------------------------------------------

@@ -35,7 +35,7 @@ class FuraxError(RuntimeError):
 class ObsDesc(ctypes.Structure):
     _fields_ = [("n_obs", ctypes.c_int32), ("ndet", ctypes.c_void_p), ("nsamp", ctypes.c_void_p),
                 ("nside", ctypes.c_void_p), ("q_bore", ctypes.c_void_p), ("q_det", ctypes.c_void_p),
-                ("psi_offset", ctypes.c_void_p), ("hwp_angle", ctypes.c_void_p)]
+                ("psi_offset", ctypes.c_void_p), ("hwp_angle", ctypes.c_void_p), ("map_id", ctypes.c_void_p)]
 
 
 class CgOpts(ctypes.Structure):
@@ -166,22 +166,26 @@ def default_cg_opts() -> CgOpts:
 class _Desc:
     """Keeps the host arrays of an ObsDesc alive."""
 
-    def __init__(self, ndet, nsamp, nside, q_bore=None, q_det=None, psi_offset=None, hwp_angle=None):
+    def __init__(self, ndet, nsamp, nside, q_bore=None, q_det=None, psi_offset=None, hwp_angle=None, map_id=None):
         self.n = len(ndet)
         self.ndet = (ctypes.c_int32 * self.n)(*[int(v) for v in ndet])
         self.nsamp = (ctypes.c_int64 * self.n)(*[int(v) for v in nsamp])
         self.nside = (ctypes.c_int32 * self.n)(*[int(v) for v in nside])
+        self.map_id = None if map_id is None else (ctypes.c_int32 * self.n)(*[int(v) for v in map_id])
         self.desc = ObsDesc(self.n, ctypes.cast(self.ndet, _V), ctypes.cast(self.nsamp, _V),
-                            ctypes.cast(self.nside, _V), q_bore, q_det, psi_offset, hwp_angle)
+                            ctypes.cast(self.nside, _V), q_bore, q_det, psi_offset, hwp_angle,
+                            None if self.map_id is None else ctypes.cast(self.map_id, _V))
 
 
 # ------------------------------------------------------------------ entry points, same names as the C ABI
 def furax_pointing_create(q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode=FURAX_POINTING_CACHE_F32,
-                          stream=None, hwp_angle=None) -> int:
+                          stream=None, hwp_angle=None, map_id=None) -> int:
     nb, nd = sum(int(v) for v in nsamp), sum(int(v) for v in ndet)
+    if map_id is not None and len(map_id) != len(ndet):
+        raise ValueError("map_id needs one entry per observation")
     d = _Desc(ndet, nsamp, nside, _ptr(q_bore, torch.float64, 4 * nb, "q_bore"),
               _ptr(q_det, torch.float64, 4 * nd, "q_det"), _ptr(psi_offset, torch.float64, nd, "psi_offset"),
-              _ptr(hwp_angle, torch.float64, nb, "hwp_angle"))
+              _ptr(hwp_angle, torch.float64, nb, "hwp_angle"), map_id)
     h = _V()
     _call("furax_pointing_create", ctypes.byref(d.desc), mode, _stream(stream), ctypes.byref(h))
     return h.value

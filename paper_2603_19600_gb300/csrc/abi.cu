@@ -3,6 +3,7 @@
 #include <cmath>
 #include <mutex>
 #include <atomic>
+#include <unordered_map>
 #include <unordered_set>
 
 #include "internal.cuh"
@@ -120,24 +121,39 @@ void prof_flush()
 using namespace fx;
 
 namespace fx {
+// Observations sharing a map_id share one map (and its pixel tiles): they carry the offset and
+// pixel-tile range of the map, whose tiles name the first of them. The PCG's per-observation
+// scalars are then the per-map scalars, computed identically for each observation of the map.
 void build_layout(const furax_obs_desc *desc, Layout &L)
 {
     int64_t det = 0, bore = 0, tod = 0, map = 0, ptile = 0;
+    std::unordered_map<int32_t, int> first_of;   // map_id -> first observation with it
     for (int i = 0; i < desc->n_obs; ++i) {
         ObsInfo o{};
         o.nsamp = desc->nsamp[i];
         o.ndet = desc->ndet[i];
         o.nside = desc->nside[i];
         o.npix = 12LL * o.nside * o.nside;
-        o.det_off = det; o.bore_off = bore; o.tod_off = tod; o.map_off = map;
-        o.ptile0 = ptile;
-        o.nptile = (int32_t)((o.npix + PTILE - 1) / PTILE);
-        for (int64_t k = 0; k < o.nptile; ++k) {
-            PTile t;
-            t.p0 = map + k * PTILE;
-            t.obs = i;
-            t.len = (int32_t)std::min<int64_t>(PTILE, o.npix - k * PTILE);
-            L.ptiles.push_back(t);
+        o.det_off = det; o.bore_off = bore; o.tod_off = tod;
+        int owner = i;
+        if (desc->map_id) owner = first_of.emplace(desc->map_id[i], i).first->second;
+        if (owner != i) {
+            o.map_off = L.obs[owner].map_off;
+            o.ptile0 = L.obs[owner].ptile0;
+            o.nptile = L.obs[owner].nptile;
+        } else {
+            o.map_off = map;
+            o.ptile0 = ptile;
+            o.nptile = (int32_t)((o.npix + PTILE - 1) / PTILE);
+            for (int64_t k = 0; k < o.nptile; ++k) {
+                PTile t;
+                t.p0 = map + k * PTILE;
+                t.obs = i;
+                t.len = (int32_t)std::min<int64_t>(PTILE, o.npix - k * PTILE);
+                L.ptiles.push_back(t);
+            }
+            map += o.npix;
+            ptile += o.nptile;
         }
         // Time-major order: the CTAs resident at any moment process every detector over the
         // same stretch of time, i.e. one compact swath of sky, so the map gathers and the
@@ -150,7 +166,7 @@ void build_layout(const furax_obs_desc *desc, Layout &L)
                 t.pad = 0;
                 L.tiles.push_back(t);
             }
-        det += o.ndet; bore += o.nsamp; tod += o.ndet * o.nsamp; map += o.npix; ptile += o.nptile;
+        det += o.ndet; bore += o.nsamp; tod += o.ndet * o.nsamp;
         L.max_ndet = std::max(L.max_ndet, o.ndet);
         L.obs.push_back(o);
     }
@@ -264,6 +280,14 @@ static furax_status check_desc(const furax_obs_desc *d)
         REQUIRE(d->ndet[i] >= 1, "ndet[%d] = %d must be >= 1", i, d->ndet[i]);
         REQUIRE(d->nsamp[i] >= 1, "nsamp[%d] = %lld must be >= 1", i, (long long)d->nsamp[i]);
         REQUIRE(d->nside[i] >= 1 && d->nside[i] <= 8192, "nside[%d] = %d must be in [1, 8192]", i, d->nside[i]);
+    }
+    if (d->map_id) {
+        std::unordered_map<int32_t, int> first_of;
+        for (int i = 0; i < d->n_obs; ++i) {
+            const int j = first_of.emplace(d->map_id[i], i).first->second;
+            REQUIRE(d->nside[j] == d->nside[i], "observations %d and %d share map %d but have nside %d and %d", j, i,
+                    d->map_id[i], d->nside[j], d->nside[i]);
+        }
     }
     return FURAX_OK;
 }

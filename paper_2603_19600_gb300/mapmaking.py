@@ -31,16 +31,17 @@ class Pointing:
     """
 
     def __init__(self, q_bore, q_det, ndet, nsamp, nside, psi_offset=None, mode="cache_f32", stream=None,
-                 hwp_angle=None):
+                 hwp_angle=None, map_id=None):
         self.ndet, self.nsamp, self.nside = [list(map(int, v)) for v in (ndet, nsamp, nside)]
         self.q_bore = q_bore.contiguous()
         self.q_det = q_det.contiguous()
         self.mode = mode
         self.handle = None
         self.has_hwp = hwp_angle is not None
+        self.map_id = None if map_id is None else [int(v) for v in map_id]
         self.handle = nat.furax_pointing_create(self.q_bore, self.q_det, self.ndet, self.nsamp, self.nside,
                                                 psi_offset, _MODES[mode], stream,
-                                                None if hwp_angle is None else hwp_angle.contiguous())
+                                                None if hwp_angle is None else hwp_angle.contiguous(), self.map_id)
         info = nat.furax_pointing_info(self.handle)
         self.nsamp_total = info["nsamp_total"]
         self.npix_total = info["npix_total"]
@@ -63,8 +64,15 @@ class Pointing:
         hwp = None
         if hw[0] is not None:
             hwp = torch.cat([torch.as_tensor(h) for h in hw]).to(device, torch.float64)
+        ids = [getattr(o, "map_id", None) for o in observations]
+        map_id = None
+        if any(m is not None for m in ids):
+            # an observation without a map_id keeps a map of its own
+            used = {m for m in ids if m is not None}
+            fresh = iter(k for k in range(-1, -10 ** 9, -1) if k not in used)
+            map_id = [m if m is not None else next(fresh) for m in ids]
         return cls(qb, qd, [o.q_det.shape[0] for o in observations], [o.q_bore.shape[0] for o in observations],
-                   [o.nside for o in observations], psi, mode, stream, hwp)
+                   [o.nside for o in observations], psi, mode, stream, hwp, map_id)
 
     def close(self):
         if self.handle:

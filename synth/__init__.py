@@ -176,6 +176,7 @@ class Observation:
     q_det: np.ndarray            # [ndet][4] float64
     psi_offset: np.ndarray | None = None  # [ndet] rad
     hwp: np.ndarray | None = None         # [nsamp] half-wave-plate angle (rad) per boresight sample
+    map_id: int | None = None             # observations with equal map_id share one map
 
     @property
     def ndet(self) -> int:
