@@ -325,6 +325,40 @@ def deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps: int, orde
             "apply_gsamples_per_s_deprojected": S / (apply_ms["deprojected"] / 1e3) / 1e9}
 
 
+def long_band(fx, dev, stream, wl, q_bore, q_det, ntaps: int = 1024, reps: int = 5):
+    """N^-1 with a 1024-tap band (overlap-save, TOD in HBM) on the same 256 x 2^20 TOD, and the
+    normal operator built on it (P, N^-1, P^T as three passes): per-application times."""
+    import torch
+    nside, nd, ns = wl["nside"], wl["ndet"], wl["nsamp"]
+    S = nd * ns
+    taps = np.tile(synth.inverse_noise_taps(ntaps), (nd, 1))
+    out = {"workload": f"same scan, {ntaps}-tap symmetric band N^-1 by overlap-save (8192-point transforms)",
+           "ntaps": ntaps}
+    with torch.cuda.stream(stream):
+        P = fx.Pointing(q_bore, q_det, [nd], [ns], [nside], mode="cache_f32", stream=stream)
+        N = fx.Noise.banded(P, taps)
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 606)
+        x = torch.randn(S, generator=g, device=dev, dtype=torch.float32)
+        y = torch.empty_like(x)
+        m = torch.randn(P.npix_total, 3, generator=g, device=dev, dtype=torch.float64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for name, fn in (("ninv_ms", lambda: N.inv_apply(x, y)),
+                         ("apply_ms", lambda: fx.ptnp_apply(P, N, m, None, "f32", "f32"))):
+            fn()
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+            out[name] = e0.elapsed_time(e1) / reps
+        P.close()
+    out["ninv_gsamples_per_s"] = S / (out["ninv_ms"] / 1e3) / 1e9
+    out["ninv_hbm_gbs"] = 8.0 * S / (out["ninv_ms"] / 1e3) / 1e9   # FP32 TOD read + write
+    out["apply_gsamples_per_s"] = S / (out["apply_ms"] / 1e3) / 1e9
+    return out
+
+
 def batched_c4(fx, dev, stream, steps: int, joint: bool = False):
     """The batched configuration: 64 independent observations, lengths uniform in [2^18, 2^22],
     8-128 detectors, nside 256/512 alternating (9.75 G samples), one launch per operator over the
@@ -612,7 +646,8 @@ def main():
         out["hwp"] = hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps=max(1, min(args.steps, 3)))
     # ---------------- the other configurations of the workload: batched, precision, gradients
     if rank == 0 and world == 1 and not args.no_extra and not args.small:
-        for key, fn in (("deproject", lambda: deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps,
+        for key, fn in (("long_band", lambda: long_band(fx, dev, stream, wl, q_bore, q_det)),
+                        ("deproject", lambda: deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps,
                                                               steps=max(1, min(args.steps, 3)))),
                         ("precision_sweep", lambda: precision_sweep(fx, dev, stream)),
                         ("gradient", lambda: gradient_c5(fx, dev, stream)),

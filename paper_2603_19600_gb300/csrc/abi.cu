@@ -495,7 +495,7 @@ furax_status furax_noise_create(int32_t kind, const double *params, int32_t ntap
     REQUIRE(kind == FURAX_NOISE_WHITE || kind == FURAX_NOISE_BANDED, "unknown noise kind %d", kind);
     REQUIRE(params && is_device_ptr(params), "params must be device memory");
     if (kind == FURAX_NOISE_BANDED)
-        REQUIRE(ntaps >= 1 && ntaps <= MAXTAPS, "ntaps = %d must be in [1, %d]", ntaps, MAXTAPS);
+        REQUIRE(ntaps >= 1 && ntaps <= kLongTaps, "ntaps = %d must be in [1, %d]", ntaps, kLongTaps);
     else
         ntaps = 1;
     Layout L;
@@ -532,9 +532,9 @@ furax_status furax_noise_create(int32_t kind, const double *params, int32_t ntap
     noise_prep_kernel<<<(unsigned)((m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(kind, params, cnt, ntaps, n->p64,
                                                                                     n->p32, n->diag, ndet);
     count_launches(1);
-    if ((rc = check_launch("noise create"))) {
-        cudaFree(n->p64); cudaFree(n->p32); cudaFree(n->diag); cudaFree(n->d_obs); cudaFree(n->d_tiles);
-        delete n;
+    if (!(rc = check_launch("noise create")) && long_band(n)) rc = prepare_noise_fft(n, L.obs, (cudaStream_t)stream);
+    if (rc) {
+        furax_noise_destroy(n);
         return rc;
     }
     *out = n;
@@ -546,6 +546,7 @@ furax_status furax_noise_destroy(furax_noise_t *n)
     if (!n) return FURAX_OK;
     cudaDeviceSynchronize();
     cudaFree(n->p64); cudaFree(n->p32); cudaFree(n->diag); cudaFree(n->d_obs); cudaFree(n->d_tiles);
+    cudaFree(n->fft_items); cudaFree(n->tw64); cudaFree(n->tw32); cudaFree(n->spec64); cudaFree(n->spec32);
     delete n;
     return check_launch("noise destroy");
 }
@@ -605,8 +606,13 @@ furax_status furax_rhs(const furax_pointing_t *p, const furax_noise_t *n, const 
     const bool prof = prof_on();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) { prof_pair(&e0, &e1); if (e0) cudaEventRecord(e0, st); }
-    // FP64-accurate on FP32 pipes (double-FP32 band product); FP64 arithmetic would be ~5x slower here
-    if ((rc = launch_fused_df(p, n, nullptr, d, d_t, pm->ws_acc64, st))) return rc;
+    // FP64-accurate on FP32 pipes (double-FP32 band product); FP64 arithmetic would be ~5x slower here.
+    // A band longer than the fused kernels hold: overlap-save N^-1 in FP64 with the TOD in HBM.
+    if (long_band(n)) {
+        if ((rc = tod_ws(p)) || (rc = launch_rhs_chain(p, n, d, d_t, pm->ws_acc64, st))) return rc;
+    } else if ((rc = launch_fused_df(p, n, nullptr, d, d_t, pm->ws_acc64, st))) {
+        return rc;
+    }
     if (prof) { if (e1) cudaEventRecord(e1, st); prof_push(2, e0, e1); }
     return launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, pm->ws_acc64, valid, b, st);
 }
@@ -720,6 +726,7 @@ furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, 
     if (rc) return rc;
     REQUIRE(d && m && chi2, "d, m and chi2 must be device pointers");
     REQUIRE(valid_dtype(d_t) && valid_dtype(precision), "unknown dtype");
+    REQUIRE(!long_band(n), "chi2 and its gradients take bands of at most %d taps", MAXTAPS);
     return launch_chi2_grad(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, (cudaStream_t)stream);
 }
 

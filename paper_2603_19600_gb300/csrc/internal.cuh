@@ -13,7 +13,8 @@ namespace fx {
 
 constexpr int TILE = 4096;      // samples per work tile (one detector, contiguous in time)
 constexpr int PTILE = 4096;     // pixels per pixel tile (vector kernels, per-observation reductions)
-constexpr int MAXTAPS = 64;     // longest supported symmetric band (c_0..c_63)
+constexpr int MAXTAPS = 64;     // longest band of the fused kernels (c_0..c_63)
+constexpr int kLongTaps = 2048; // longest band of the overlap-save N^-1 (TOD in HBM)
 
 struct ObsInfo {
     int64_t nsamp;     // samples per detector
@@ -35,6 +36,12 @@ struct Tile {          // one detector, samples [t0, t0+len)
     int32_t det;       // local detector index within the observation
     int32_t len;
     int32_t pad;
+};
+
+struct FftItem {       // two consecutive overlap-save blocks of one detector stream
+    int64_t q0;        // first block index
+    int32_t obs;
+    int32_t det;       // local detector index within the observation
 };
 
 struct PTile {         // pixels [p0, p0+len) of one observation (global map indices)
@@ -173,6 +180,13 @@ struct furax_noise {
     fx::ObsInfo *d_obs = nullptr;     // TOD layout for the standalone N^-1
     fx::Tile *d_tiles = nullptr;
     int64_t n_tiles = 0;
+    // bands longer than MAXTAPS: overlap-save blocks, twiddles, spectra (bit-reversed order)
+    fx::FftItem *fft_items = nullptr;
+    int64_t n_fft_items = 0;
+    double2 *tw64 = nullptr;
+    float2 *tw32 = nullptr;
+    double *spec64 = nullptr;   // [ndet][8192]
+    float *spec32 = nullptr;
     fx::NoiseView view() const { return fx::NoiseView{kind, ntaps, p64, p32, diag}; }
 };
 
@@ -196,6 +210,20 @@ furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rco
 
 // ---- launchers (noise.cu)
 furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st);
+// Bands longer than the fused kernels hold go through the TOD in HBM (overlap-save N^-1).
+inline bool long_band(const furax_noise *n) { return n->kind == FURAX_NOISE_BANDED && n->ntaps > MAXTAPS; }
+// noise_fft.cu: blocks, twiddles and spectra of a long band (synchronises st); the N^-1 apply.
+furax_status prepare_noise_fft(furax_noise *n, const std::vector<ObsInfo> &obs, cudaStream_t st);
+furax_status launch_ninv_fft(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st);
+// acc64 += P^T tod (FP64 accumulation into the caller's [npix][3] accumulator; pointing.cu).
+furax_status launch_PT_acc64(const furax_pointing *p, const void *tod, int tod_t, double *acc64, cudaStream_t st);
+// The normal operator and right-hand side with the TOD in HBM (solver.cu): acc64 += P^T N^-1 P x
+// (TOD in tod_t) and acc64 += P^T N^-1 d (FP64 TOD). The TOD workspaces must exist (tod_ws).
+furax_status tod_ws(const furax_pointing *p);
+furax_status launch_ata_chain(const furax_pointing *p, const furax_noise *n, const double *x, int tod_t,
+                              double *acc64, cudaStream_t st);
+furax_status launch_rhs_chain(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *acc64,
+                              cudaStream_t st);
 // Observation table, time tiles and pixel tiles of a batch.
 struct Layout {
     std::vector<ObsInfo> obs;

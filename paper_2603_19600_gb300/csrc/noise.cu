@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(FT) ninv_kernel(const Tile *__restrict__ tiles
 
 furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st)
 {
+    if (long_band(n)) return launch_ninv_fft(n, in, out, dtype, st);
     if (n->n_tiles == 0) return FURAX_OK;
     const unsigned g = (unsigned)n->n_tiles;
     const NoiseView nv = n->view();

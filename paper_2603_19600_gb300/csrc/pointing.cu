@@ -229,6 +229,17 @@ static void dispatch_PT(const furax_pointing *p, const void *tod, int tod_t, int
     else dispatch_PT_acc<MODE, FURAX_ACC_F32_KAHAN>(p, tod, tod_t, hi, lo, a64, hits, st);
 }
 
+furax_status launch_PT_acc64(const furax_pointing *p, const void *tod, int tod_t, double *acc64, cudaStream_t st)
+{
+    if (p->n_tiles == 0) return FURAX_OK;
+    if (p->mode == FURAX_POINTING_ON_THE_FLY) dispatch_PT<0>(p, tod, tod_t, FURAX_ACC_F64, nullptr, nullptr, acc64, nullptr, st);
+    else if (p->mode == FURAX_POINTING_CACHE_F32) dispatch_PT<1>(p, tod, tod_t, FURAX_ACC_F64, nullptr, nullptr, acc64, nullptr, st);
+    else if (p->mode == FURAX_POINTING_CACHE_MIXED) dispatch_PT<3>(p, tod, tod_t, FURAX_ACC_F64, nullptr, nullptr, acc64, nullptr, st);
+    else dispatch_PT<2>(p, tod, tod_t, FURAX_ACC_F64, nullptr, nullptr, acc64, nullptr, st);
+    count_launches(1);
+    return check_launch("pointing transpose");
+}
+
 furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void *map, int map_t, int acc,
                        int32_t *hits, int accumulate, cudaStream_t st)
 {

@@ -154,6 +154,45 @@ furax_status launch_mask_copy(const furax_pointing *p, const double *x, const ui
     return check_launch("mask copy");
 }
 
+__global__ void tod_to_f64_kernel(const float *__restrict__ in, double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+furax_status tod_ws(const furax_pointing *p)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(1, p->nsamp_total);
+    furax_status rc = ensure_ws(pm, &pm->ws_tod, bytes);
+    if (!rc) rc = ensure_ws(pm, &pm->ws_tod2, bytes);
+    return rc;
+}
+
+furax_status launch_ata_chain(const furax_pointing *p, const furax_noise *n, const double *x, int tod_t,
+                              double *acc64, cudaStream_t st)
+{
+    furax_status rc;
+    if ((rc = launch_P(p, x, FURAX_F64, p->ws_tod, tod_t, st))) return rc;
+    if ((rc = launch_ninv(n, p->ws_tod, p->ws_tod2, tod_t, st))) return rc;
+    return launch_PT_acc64(p, p->ws_tod2, tod_t, acc64, st);
+}
+
+furax_status launch_rhs_chain(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *acc64,
+                              cudaStream_t st)
+{
+    furax_status rc;
+    const void *d64 = d;
+    if (d_t == FURAX_F32) {
+        tod_to_f64_kernel<<<vgrid(p->nsamp_total), VT, 0, st>>>((const float *)d, (double *)p->ws_tod, p->nsamp_total);
+        count_launches(1);
+        if ((rc = check_launch("TOD to FP64"))) return rc;
+        d64 = p->ws_tod;
+    }
+    if ((rc = launch_ninv(n, d64, p->ws_tod2, FURAX_F64, st))) return rc;
+    return launch_PT_acc64(p, p->ws_tod2, FURAX_F64, acc64, st);
+}
+
 // out = S P^T N^-1 P S^T x
 furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const double *x, double *out,
                         const uint8_t *valid, int precision, int acc, cudaStream_t st, const furax_templates *tp)
@@ -161,6 +200,24 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     const int64_t np = p->npix_total;
     furax_status rc;
+    if (long_band(n)) {
+        // the band does not fit the fused kernels: P, overlap-save N^-1 and P^T with the TOD in HBM,
+        // FP64 accumulation (FP32 TOD for precision FURAX_F32)
+        if ((rc = tod_ws(p))) return rc;
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc64, sizeof(double) * 3 * np))) return rc;
+        const double *xin = x;
+        if (valid) {
+            if ((rc = ensure_ws(pm, (void **)&pm->ws_x64, sizeof(double) * 3 * np))) return rc;
+            if ((rc = launch_mask_copy(p, x, valid, pm->ws_x64, st))) return rc;
+            xin = pm->ws_x64;
+        }
+        if ((rc = check_cuda(cudaMemsetAsync(pm->ws_acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
+        const int tod_t = precision == FURAX_F32 ? FURAX_F32 : FURAX_F64;
+        if ((rc = launch_ata_chain(p, n, xin, tod_t, pm->ws_acc64, st))) return rc;
+        if (tp && (rc = launch_tpl_map(tp, FURAX_F64, FURAX_ACC_F64, nullptr, xin, nullptr, nullptr, pm->ws_acc64, st)))
+            return rc;
+        return launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, pm->ws_acc64, valid, out, st);
+    }
     if (precision == FURAX_F64 || precision == FURAX_PREC_F32X2) {
         if ((rc = ensure_ws(pm, (void **)&pm->ws_acc64, sizeof(double) * 3 * np))) return rc;
         const double *xin = x;
@@ -504,7 +561,13 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
     furax_status rc;
     int acc = b.acc;
     if (e0) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);  // a timing node inside a captured graph
-    if (b.precision == FURAX_F64) {
+    const bool lb = long_band(b.n);
+    if (lb) {
+        // TOD in HBM; FP32 TOD for the inner solve of the mixed precision, FP64 accumulation
+        if ((rc = launch_ata_chain(p, b.n, w->p, b.precision == FURAX_F64 ? FURAX_F64 : FURAX_F32, w->acc64, st)))
+            return rc;
+        acc = FURAX_ACC_F64;
+    } else if (b.precision == FURAX_F64) {
         if ((rc = launch_fused_f64(p, b.n, w->p, w->acc64, st))) return rc;
         acc = FURAX_ACC_F64;
     } else {
@@ -513,7 +576,7 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     if (b.tp) {
-        const bool f64 = b.precision == FURAX_F64;
+        const bool f64 = b.precision == FURAX_F64 || lb;
         if ((rc = launch_tpl_map(b.tp, f64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi, w->lo, w->acc64, st,
                                  !f64 && tpl_fused_target(b.tp, p) != nullptr)))
             return rc;
@@ -547,8 +610,10 @@ static furax_status body_prologue(const Body &b, cudaStream_t st)
 
 static int64_t graph_nodes_per_iter(const Body &b)
 {
-    if (!b.tp) return 6;
-    return b.precision != FURAX_F64 && tpl_fused_target(b.tp, b.p) ? 8 : 9;
+    const bool lb = long_band(b.n);
+    int64_t k = 5 + (lb ? 3 : 1);
+    if (b.tp) k += (!lb && b.precision != FURAX_F64 && tpl_fused_target(b.tp, b.p)) ? 2 : 3;
+    return k;
 }
 
 // Run PCG from b (in w->bfull or a given rhs) into x. Returns iterations used (max over obs).
@@ -648,7 +713,9 @@ static furax_status true_residual(const Body &b, const double *x, double *rtrue,
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * p->npix_total, st), "memset"))) return rc;
     // The plain FP64 solve checks itself with the FP64 operator; the mixed solve with the
     // FP64-accurate double-FP32 operator (same system, ~2^-48 arithmetic, FP32 pipes).
-    if (b.precision == FURAX_F64) {
+    if (long_band(b.n)) {
+        if ((rc = launch_ata_chain(p, b.n, x, FURAX_F64, w->acc64, st))) return rc;
+    } else if (b.precision == FURAX_F64) {
         if ((rc = timed(1, st, [&] { return launch_fused_f64(p, b.n, x, w->acc64, st); }))) return rc;
     } else {
         if ((rc = timed(2, st, [&] { return launch_fused_df(p, b.n, x, nullptr, 0, w->acc64, st); }))) return rc;
@@ -686,7 +753,11 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     if ((rc = launch_bj(p, n, o->rcond_min, w->minv, w->valid, nullptr, nullptr, st))) return rc;
     // Right-hand side b = S P^T N^-1 d in FP64.
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
-    if (o->precision == FURAX_F64) {
+    if (long_band(n)) {
+        // TOD workspaces exist before any stream capture of the iteration
+        if ((rc = tod_ws(p))) return rc;
+        if ((rc = launch_rhs_chain(p, n, d, d_t, w->acc64, st))) return rc;
+    } else if (o->precision == FURAX_F64) {
         if ((rc = timed(1, st, [&] { return launch_rhs_f64(p, n, d, d_t, w->acc64, st); }))) return rc;
     } else {
         if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, nullptr, d, d_t, w->acc64, st); }))) return rc;
@@ -696,7 +767,8 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     if (valid_out && (rc = check_cuda(cudaMemcpyAsync(valid_out, w->valid, np, cudaMemcpyDeviceToDevice, st), "copy mask")))
         return rc;
 
-    Body b{p, n, w, o->precision, o->acc, o->tol * o->tol, x, pg, tp};
+    // a long band accumulates in FP64 (its operator goes through the TOD in HBM)
+    Body b{p, n, w, o->precision, long_band(n) ? FURAX_ACC_F64 : o->acc, o->tol * o->tol, x, pg, tp};
     int total_iters = 0, outer = 0;
     bool converged = false;
     double rel = 0.0, true_rel = 0.0;

@@ -357,7 +357,7 @@ static void solve(const furax_templates *tp, cudaStream_t st)
 
 double *tpl_fused_target(const furax_templates *tp, const furax_pointing *p)
 {
-    return tp && fused_f32_projects_templates(p) ? tp->a : nullptr;
+    return tp && !long_band(tp->n) && fused_f32_projects_templates(p) ? tp->a : nullptr;
 }
 
 furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, const float4 *x32, const double *x64,
