@@ -159,15 +159,15 @@ bool fused_f32_projects_templates(const furax_pointing *p)
 }
 
 furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                              float4 *lo, double *a64, cudaStream_t st, double *tpl_a)
+                              float4 *lo, double *a64, cudaStream_t st, const FusedTpl *ft)
 {
     if (p->n_tiles == 0) return FURAX_OK;
     furax_status rc;
-    if (tpl_a && !fused_f32_projects_templates(p))
-        return set_error(FURAX_EINVAL, "the template projection is fused only for the cached FP32 pointing");
+    if (ft && !fused_f32_projects_templates(p))
+        return set_error(FURAX_EINVAL, "template work is fused only for the cached FP32 pointing");
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
     else if (p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED)  // FP32 weights: hi
-        rc = launch_fused_tma(p, n, x32, acc, hi, lo, a64, st, tpl_a);
+        rc = launch_fused_tma(p, n, x32, acc, hi, lo, a64, st, ft);
     else rc = dispatch_fused_f32<2>(p, n, x32, acc, hi, lo, a64, st);
     if (rc) return rc;
     count_launches(1);

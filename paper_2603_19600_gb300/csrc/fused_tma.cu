@@ -44,6 +44,7 @@ struct TmaSmem {
     float s[kRawStages][kRawN];
     float xs[kXsStages][XS];
     alignas(16) float taps[kXsStages][2 * kBandPad];   // band in tap order as (c_|j-63|, c_|j-63|) pairs
+    float4 amp[kRawStages];                            // TPL 2: the tile detector's template amplitudes
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
@@ -108,14 +109,18 @@ __device__ __forceinline__ TileSpan tile_span(const Tile &tl, const ObsInfo &ob,
     return sp;
 }
 
-// With TPL the consumers also accumulate T^T z per detector into tpl_a[det][4] (z = N^-1 P x
-// of the tile's samples, T = Legendre P_0..P_3 of tau_t = 2t/(ns-1) - 1): the projection of the
-// template-deprojected operator, which then needs no pass of its own.
-template <int ACC, bool BANDED, bool TPL>
+// Template work (T = Legendre P_0.. of tau_t = 2t/(ns-1) - 1 per detector, z = N^-1 u of the
+// tile's samples):
+//   TPL 1: the consumers add T^T z (P_0..P_3) to tpl.proj[det][4], the projection of the
+//          template-deprojected operator, which then needs no pass of its own;
+//   TPL 2: the augmented system [m; a]: u_t = (P m)_t + sum_l a_l P_l(tau_t) with the detector's
+//          amplitudes a (l <= 2) read from x32[tpl.base + det], and T^T z (l <= tpl.order)
+//          accumulated into the amplitude pseudo-pixel tpl.base + det like a pixel.
+template <int ACC, bool BANDED, int TPL>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     fused_tma_kernel(const Tile *__restrict__ tiles, int64_t n_tiles, PointingView pv, NoiseView nv,
                      const float4 *__restrict__ x32, float4 *__restrict__ acc_hi, float4 *__restrict__ acc_lo,
-                     double *__restrict__ acc64, unsigned *__restrict__ err, double *__restrict__ tpl_a)
+                     double *__restrict__ acc64, unsigned *__restrict__ err, FusedTpl tpl)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     TmaSmem &S = *reinterpret_cast<TmaSmem *>(tsm);
@@ -140,6 +145,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const ObsInfo ob = pv.obs[tl.obs];
             const TileSpan sp = tile_span(tl, ob, halo);
             const uint32_t bytes = (uint32_t)sp.n * 4u;
+            // written before the arrive below, which releases it to the threads waiting on the stage
+            if constexpr (TPL == 2) S.amp[r] = x32[tpl.base + ob.det_off + tl.det];
             mbar_expect_tx(&S.raw_full[r], 3u * bytes);
             bulk_g2s(S.pix[r], pv.pix + sp.g0, bytes, &S.raw_full[r]);
             bulk_g2s(S.c[r], pv.c32 + sp.g0, bytes, &S.raw_full[r]);
@@ -198,6 +205,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     S.xs[q][spos(u)] = v;
                 }
             }
+            if constexpr (TPL == 2) {
+                // the templates act on every sample of the stream; a second pass over this
+                // thread's own slots keeps the loads above free of extra live registers
+                const float4 amp = S.amp[r];
+                const float h = ob.nsamp > 1 ? 2.f / (float)(ob.nsamp - 1) : 0.f;
+                const float tau0 = ob.nsamp > 1 ? (float)t_first * h - 1.f : 0.f;
+#pragma unroll 4
+                for (int k = 0; k < kGatherPer; ++k) {
+                    const int u = tid + k * 32 * kTmaGather;
+                    const int64_t t = t_first + u;
+                    if (u < nload && t >= 0 && t < ob.nsamp) {
+                        const float tau = fmaf((float)u, h, tau0);
+                        S.xs[q][spos(u)] += fmaf(amp.z, 1.5f * tau * tau - 0.5f, fmaf(amp.y, tau, amp.x));
+                    }
+                }
+            }
             mbar_arrive(&S.xs_full[q]);
         }
         return;
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         // Every consumer has read its stencil inputs: y overwrites the stage in place (core
         // sample u at slot spos(u)), which is released to the gathers after the scatter.
         if (!consumers_all(ok)) break;
-        if constexpr (TPL) {
+        if constexpr (TPL != 0) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             if (base < tl.len) {
                 const float h = ob.nsamp > 1 ? 2.f / (float)(ob.nsamp - 1) : 0.f;
@@ -245,9 +268,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             for (int l = 0; l < 4; ++l)
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a[l] += __shfl_down_sync(0xffffffffu, a[l], o);
-            if ((threadIdx.x & 31) == 0)
+            if ((threadIdx.x & 31) == 0) {
+                if constexpr (TPL == 1) {
 #pragma unroll
-                for (int l = 0; l < 4; ++l) red_add_f64(tpl_a + 4 * gdet + l, (double)a[l]);
+                    for (int l = 0; l < 4; ++l) red_add_f64(tpl.proj + 4 * gdet + l, (double)a[l]);
+                } else {
+                    const float4 v = make_float4(a[0], tpl.order >= 1 ? a[1] : 0.f, tpl.order >= 2 ? a[2] : 0.f, 0.f);
+                    const int64_t gp = tpl.base + gdet;
+                    if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
+                    else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
+                    else {
+                        red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
+                        red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
+                        red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
+                    }
+                }
+            }
         }
         float *ys = S.xs[q];
 #pragma unroll
@@ -282,36 +318,42 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 }
 
-template <int ACC, bool BANDED, bool TPL>
+template <int ACC, bool BANDED, int TPL>
 static furax_status run_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, float4 *hi, float4 *lo,
-                            double *a64, double *tpl_a, cudaStream_t st)
+                            double *a64, const FusedTpl &ft, cudaStream_t st)
 {
     const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
     return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL>, g, kTmaThreads, kTmaSmem, st, p->d_tiles, p->n_tiles,
-                      p->view(), n->view(), x32, hi, lo, a64, p->d_err, tpl_a);
+                      p->view(), n->view(), x32, hi, lo, a64, p->d_err, ft);
 }
 
-template <bool BANDED, bool TPL>
+template <bool BANDED, int TPL>
 static furax_status dispatch_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                                 float4 *lo, double *a64, double *tpl_a, cudaStream_t st)
+                                 float4 *lo, double *a64, const FusedTpl &ft, cudaStream_t st)
 {
-    if (acc == FURAX_ACC_F32) return run_tma<FURAX_ACC_F32, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
-    if (acc == FURAX_ACC_F32_KAHAN) return run_tma<FURAX_ACC_F32_KAHAN, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
-    return run_tma<FURAX_ACC_F64, BANDED, TPL>(p, n, x32, hi, lo, a64, tpl_a, st);
+    if (acc == FURAX_ACC_F32) return run_tma<FURAX_ACC_F32, BANDED, TPL>(p, n, x32, hi, lo, a64, ft, st);
+    if (acc == FURAX_ACC_F32_KAHAN) return run_tma<FURAX_ACC_F32_KAHAN, BANDED, TPL>(p, n, x32, hi, lo, a64, ft, st);
+    return run_tma<FURAX_ACC_F64, BANDED, TPL>(p, n, x32, hi, lo, a64, ft, st);
+}
+
+template <int TPL>
+static furax_status dispatch_tma_band(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
+                                      float4 *hi, float4 *lo, double *a64, const FusedTpl &ft, cudaStream_t st)
+{
+    return n->kind == FURAX_NOISE_BANDED ? dispatch_tma<true, TPL>(p, n, x32, acc, hi, lo, a64, ft, st)
+                                         : dispatch_tma<false, TPL>(p, n, x32, acc, hi, lo, a64, ft, st);
 }
 
 furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                              float4 *lo, double *a64, cudaStream_t st, double *tpl_a)
+                              float4 *lo, double *a64, cudaStream_t st, const FusedTpl *ft)
 {
-    const bool b = n->kind == FURAX_NOISE_BANDED;
-    if (tpl_a)
-        return b ? dispatch_tma<true, true>(p, n, x32, acc, hi, lo, a64, tpl_a, st)
-                 : dispatch_tma<false, true>(p, n, x32, acc, hi, lo, a64, tpl_a, st);
-    return b ? dispatch_tma<true, false>(p, n, x32, acc, hi, lo, a64, nullptr, st)
-             : dispatch_tma<false, false>(p, n, x32, acc, hi, lo, a64, nullptr, st);
+    const FusedTpl none{0, nullptr, 0, 0};
+    if (!ft || ft->mode == 0) return dispatch_tma_band<0>(p, n, x32, acc, hi, lo, a64, none, st);
+    if (ft->mode == 1) return dispatch_tma_band<1>(p, n, x32, acc, hi, lo, a64, *ft, st);
+    return dispatch_tma_band<2>(p, n, x32, acc, hi, lo, a64, *ft, st);
 }
 
-template <bool BANDED, bool TPL>
+template <bool BANDED, int TPL>
 static furax_status prepare_tma_band()
 {
     furax_status rc = FURAX_OK;
@@ -323,10 +365,13 @@ static furax_status prepare_tma_band()
 
 furax_status prepare_fused_tma()
 {
-    furax_status rc = prepare_tma_band<true, false>();
-    if (!rc) rc = prepare_tma_band<false, false>();
-    if (!rc) rc = prepare_tma_band<true, true>();
-    if (!rc) rc = prepare_tma_band<false, true>();
+    furax_status rc = FURAX_OK;
+    if (!rc) rc = prepare_tma_band<true, 0>();
+    if (!rc) rc = prepare_tma_band<false, 0>();
+    if (!rc) rc = prepare_tma_band<true, 1>();
+    if (!rc) rc = prepare_tma_band<false, 1>();
+    if (!rc) rc = prepare_tma_band<true, 2>();
+    if (!rc) rc = prepare_tma_band<false, 2>();
     return rc;
 }
 

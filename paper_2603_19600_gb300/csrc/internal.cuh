@@ -71,6 +71,14 @@ struct NoiseView {
     const double *diag;     // diagonal of N^-1 per detector [ndet] (FP64)
 };
 
+// Template work folded into the fused FP32 operator (see fused_tma.cu).
+struct FusedTpl {
+    int mode;        // 1: add T^T N^-1 P x to proj[det][4]; 2: augmented system, amplitudes at base + det
+    double *proj;    // mode 1
+    int64_t base;    // mode 2: index of detector 0's amplitude pseudo-pixel (npix_total)
+    int order;       // highest Legendre degree
+};
+
 // Template deprojection (per-detector Legendre templates, W = N^-1).
 struct TplView {
     int32_t order;          // highest Legendre degree K (<= 3)
@@ -166,6 +174,11 @@ struct furax_templates {
     double *a = nullptr;                 // [ndet][4] projections (kept zero between uses)
     double *b = nullptr;                 // [ndet][4]
     unsigned long long *bad = nullptr;   // setup status (1 + first detector with a singular Gram matrix)
+    // Augmented layout of the inner FP32 solve (order <= 2): one amplitude pseudo-pixel per
+    // detector at npix_total + det; each map's pixel tiles followed by its detectors' pseudo tiles.
+    fx::PTile *d_aug_ptiles = nullptr;
+    fx::ObsInfo *d_aug_obs = nullptr;
+    int64_t n_aug_ptiles = 0;
     fx::TplView view() const { return fx::TplView{order, halo, mom, ginv, b}; }
 };
 
@@ -241,11 +254,11 @@ furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, con
 
 // ---- launchers (fused.cu)
 // acc_* workspaces must be zeroed by the caller; x32 is the padded FP32 copy of the (masked) input.
-// With tpl_a (cached FP32 pointing only: see fused_f32_projects_templates), the kernel also adds
-// the template projection T^T N^-1 P x per detector to tpl_a[det][4].
+// With ft (cached FP32 pointing only: see fused_f32_projects_templates), the kernel also does
+// the template work of ft->mode.
 furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc,
                               float4 *acc_hi, float4 *acc_lo, double *acc64, cudaStream_t st,
-                              double *tpl_a = nullptr);
+                              const FusedTpl *ft = nullptr);
 bool fused_f32_projects_templates(const furax_pointing *p);
 furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, const double *x, double *acc64,
                               cudaStream_t st);
@@ -284,6 +297,10 @@ furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, c
 double *tpl_fused_target(const furax_templates *tp, const furax_pointing *p);
 // acc64 -= P^T (W T) G^-1 (W T)^T d (FP64 arithmetic).
 furax_status launch_tpl_rhs(const furax_templates *tp, const void *d, int d_t, double *acc64, cudaStream_t st);
+// The inner FP32 solve runs on the augmented system [m; amplitudes] (one fused pass per iteration).
+bool tpl_augmented(const furax_templates *tp, int precision);
+// minv and valid of the amplitude pseudo-pixels: the 3x3 leading block of G^-1.
+furax_status launch_tpl_aug_precond(const furax_templates *tp, double *minv, uint8_t *valid, cudaStream_t st);
 // amp [ndet][K+1] = G^-1 (W T)^T (d - P m) (m: FP64 map, zero on masked pixels).
 furax_status tpl_amplitudes(const furax_templates *tp, const void *d, int d_t, const double *m, double *amp,
                             cudaStream_t st);

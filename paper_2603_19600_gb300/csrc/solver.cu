@@ -43,6 +43,7 @@ struct CgWs {
     int graph_iters = 0, graph_prec = -1, graph_acc = -1;
     const void *graph_noise = nullptr;
     const void *graph_tpl = nullptr;
+    const void *graph_pt = nullptr;
     const double *graph_x = nullptr;
     double graph_tol2 = -1.0;
     bool graph_prof = false;
@@ -253,7 +254,9 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
     }
     if ((rc = launch_pack_x32(p, x, valid, pm->ws_map32, hi, lo, st))) return rc;
     double *tpl_a = tpl_fused_target(tp, p);
-    if ((rc = timed(0, st, [&] { return launch_fused_f32(p, n, pm->ws_map32, acc, hi, lo, a64, st, tpl_a); })))
+    const FusedTpl ft{1, tpl_a, 0, tp ? tp->order : 0};
+    if ((rc = timed(0, st, [&] { return launch_fused_f32(p, n, pm->ws_map32, acc, hi, lo, a64, st,
+                                                         tpl_a ? &ft : nullptr); })))
         return rc;
     if (tp && (rc = launch_tpl_map(tp, FURAX_F32, acc, pm->ws_map32, nullptr, hi, lo, a64, st, tpl_a != nullptr)))
         return rc;
@@ -511,7 +514,8 @@ static furax_status get_ws(furax_pointing *p, int hist_cap, CgWs **out)
     if (p->cg && p->cg->hist_cap >= hist_cap) { *out = p->cg; return FURAX_OK; }
     if (p->cg) destroy_cg_ws(p);
     CgWs *w = new CgWs();
-    const int64_t np = p->npix_total;
+    // room for one amplitude pseudo-pixel per detector (the augmented system of template deprojection)
+    const int64_t np = p->npix_total + p->ndet_total;
     w->np = np;
     furax_status rc = FURAX_OK;
     const size_t v3 = sizeof(double) * 3 * (size_t)np;
@@ -527,7 +531,8 @@ static furax_status get_ws(furax_pointing *p, int hist_cap, CgWs **out)
     if (!rc) rc = alloc((void **)&w->p32, sizeof(float4) * (size_t)np);
     if (!rc) rc = alloc((void **)&w->hi, sizeof(float4) * (size_t)np);
     if (!rc) rc = alloc((void **)&w->lo, sizeof(float4) * (size_t)np);
-    if (!rc) rc = alloc((void **)&w->partial, sizeof(double) * KD * (size_t)std::max<int64_t>(1, p->n_ptiles));
+    const int64_t nparts = p->n_ptiles + p->n_obs + p->ndet_total / PTILE + 1;   // also the augmented tiles
+    if (!rc) rc = alloc((void **)&w->partial, sizeof(double) * KD * (size_t)nparts);
     if (!rc) rc = alloc((void **)&w->sc, sizeof(CgScalars) * p->n_obs);
     w->hist_cap = std::max(hist_cap, 1);
     if (!rc) rc = alloc((void **)&w->hist, sizeof(double) * w->hist_cap);
@@ -551,6 +556,12 @@ struct Body {
     double *x;
     unsigned pg;   // pixel-tile grid
     const furax_templates *tp;   // template deprojection, or nullptr
+    // layout of the solved vector: the pointing's pixel tiles and observations, or the augmented
+    // ones of the templates (the map plus one amplitude pseudo-pixel per detector)
+    const PTile *pt;
+    const ObsInfo *cobs;
+    int64_t np_cg;
+    bool aug;
 };
 
 // One PCG iteration: q = A p, alpha, x/r/z update, beta, new direction (+ accumulator reset).
@@ -571,22 +582,25 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
         if ((rc = launch_fused_f64(p, b.n, w->p, w->acc64, st))) return rc;
         acc = FURAX_ACC_F64;
     } else {
-        if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st, tpl_fused_target(b.tp, p))))
+        FusedTpl ft{0, nullptr, 0, 0};
+        if (b.aug) ft = FusedTpl{2, nullptr, p->npix_total, b.tp->order};
+        else if (double *pa = tpl_fused_target(b.tp, p)) ft = FusedTpl{1, pa, 0, b.tp->order};
+        if ((rc = launch_fused_f32(p, b.n, w->p32, acc, w->hi, w->lo, w->acc64, st, ft.mode ? &ft : nullptr)))
             return rc;
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
-    if (b.tp) {
+    if (b.tp && !b.aug) {
         const bool f64 = b.precision == FURAX_F64 || lb;
         if ((rc = launch_tpl_map(b.tp, f64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi, w->lo, w->acc64, st,
                                  !f64 && tpl_fused_target(b.tp, p) != nullptr)))
             return rc;
     }
-    cg_q_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
-    cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc);
-    cg_update_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
-    cg_beta_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc, b.tol2, w->hist, w->hist_cap);
+    cg_q_kernel<<<b.pg, VT, 0, st>>>(b.pt, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
+    cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(b.cobs, w->partial, w->sc);
+    cg_update_kernel<<<b.pg, VT, 0, st>>>(b.pt, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
+    cg_beta_kernel<<<p->n_obs, VT, 0, st>>>(b.cobs, w->partial, w->sc, b.tol2, w->hist, w->hist_cap);
     const bool f32 = b.precision != FURAX_F64;
-    cg_dir_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->sc, w->z, w->p, f32 ? w->p32 : nullptr,
+    cg_dir_kernel<<<b.pg, VT, 0, st>>>(b.pt, w->sc, w->z, w->p, f32 ? w->p32 : nullptr,
                                        (f32 && acc != FURAX_ACC_F64) ? w->hi : nullptr,
                                        (f32 && acc == FURAX_ACC_F32_KAHAN) ? w->lo : nullptr,
                                        (!f32 || acc == FURAX_ACC_F64) ? w->acc64 : nullptr);
@@ -600,16 +614,17 @@ static furax_status body_prologue(const Body &b, cudaStream_t st)
     CgWs *w = b.w;
     const bool f32 = b.precision != FURAX_F64;
     const int acc = f32 ? b.acc : FURAX_ACC_F64;
-    cg_pack_kernel<<<vgrid(b.p->npix_total), VT, 0, st>>>(w->p, f32 ? w->p32 : nullptr,
+    cg_pack_kernel<<<vgrid(b.np_cg), VT, 0, st>>>(w->p, f32 ? w->p32 : nullptr,
                                                           (f32 && acc != FURAX_ACC_F64) ? w->hi : nullptr,
                                                           (f32 && acc == FURAX_ACC_F32_KAHAN) ? w->lo : nullptr,
-                                                          (acc == FURAX_ACC_F64) ? w->acc64 : nullptr, b.p->npix_total);
+                                                          (acc == FURAX_ACC_F64) ? w->acc64 : nullptr, b.np_cg);
     count_launches(1);
     return check_launch("PCG prologue");
 }
 
 static int64_t graph_nodes_per_iter(const Body &b)
 {
+    if (b.aug) return 6;
     const bool lb = long_band(b.n);
     int64_t k = 5 + (lb ? 3 : 1);
     if (b.tp) k += (!lb && b.precision != FURAX_F64 && tpl_fused_target(b.tp, b.p)) ? 2 : 3;
@@ -623,8 +638,8 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
     CgWs *w = b.w;
     const furax_pointing *p = b.p;
     furax_status rc;
-    cg_init_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, rhs, w->minv, w->valid, b.x, w->r, w->z, w->p, w->partial);
-    cg_init_scalars_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, w->sc, w->hist);
+    cg_init_kernel<<<b.pg, VT, 0, st>>>(b.pt, rhs, w->minv, w->valid, b.x, w->r, w->z, w->p, w->partial);
+    cg_init_scalars_kernel<<<p->n_obs, VT, 0, st>>>(b.cobs, w->partial, w->sc, w->hist);
     count_launches(2);
     if ((rc = check_launch("PCG init"))) return rc;
     if ((rc = body_prologue(b, st))) return rc;
@@ -640,7 +655,8 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
             const bool prof = prof_on();
             const bool rebuild = !w->graph || w->graph_iters != n || w->graph_prec != b.precision ||
                                  w->graph_acc != b.acc || w->graph_noise != (const void *)b.n || w->graph_x != b.x ||
-                                 w->graph_tol2 != b.tol2 || w->graph_prof != prof || w->graph_tpl != (const void *)b.tp;
+                                 w->graph_tol2 != b.tol2 || w->graph_prof != prof || w->graph_tpl != (const void *)b.tp ||
+                                 w->graph_pt != (const void *)b.pt;
             if (rebuild) {
                 if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
                 while (prof && (int)w->ev.size() < 2 * n) {
@@ -664,6 +680,7 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
                 if ((rc = check_cuda(e, "graph instantiate"))) return rc;
                 w->graph_iters = n; w->graph_prec = b.precision; w->graph_acc = b.acc; w->graph_noise = b.n;
                 w->graph_x = b.x; w->graph_tol2 = b.tol2; w->graph_prof = prof; w->graph_tpl = b.tp;
+                w->graph_pt = b.pt;
             }
             if ((rc = check_cuda(cudaGraphLaunch(w->graph, st), "graph launch"))) return rc;
             count_launches(graph_nodes_per_iter(b) * n);
@@ -768,7 +785,8 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
         return rc;
 
     // a long band accumulates in FP64 (its operator goes through the TOD in HBM)
-    Body b{p, n, w, o->precision, long_band(n) ? FURAX_ACC_F64 : o->acc, o->tol * o->tol, x, pg, tp};
+    Body b{p, n, w, o->precision, long_band(n) ? FURAX_ACC_F64 : o->acc, o->tol * o->tol, x, pg, tp,
+           p->d_ptiles, p->d_obs, np, false};
     int total_iters = 0, outer = 0;
     bool converged = false;
     double rel = 0.0, true_rel = 0.0;
@@ -802,8 +820,23 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
         Body bi = b;
         bi.x = w->e;
         bi.tol2 = o->inner_tol * o->inner_tol;
+        const int64_t npseudo = 3 * p->ndet_total;   // amplitude entries of the augmented system
+        if (tpl_augmented(tp, o->precision)) {
+            bi.aug = true;
+            bi.pt = tp->d_aug_ptiles;
+            bi.cobs = tp->d_aug_obs;
+            bi.pg = (unsigned)std::max<int64_t>(1, tp->n_aug_ptiles);
+            bi.np_cg = np + p->ndet_total;
+            if ((rc = launch_tpl_aug_precond(tp, w->minv, w->valid, st))) return rc;
+            if ((rc = check_cuda(cudaMemsetAsync(w->bfull + 3 * np, 0, sizeof(double) * npseudo, st), "memset")))
+                return rc;
+        }
         while (outer < o->max_outer && total_iters < o->maxiter) {
             const double *rhs_in = outer == 0 ? w->bfull : w->r;
+            // the augmented right-hand side is [r; 0]: r's amplitude part holds the last inner residual
+            if (bi.aug && outer > 0 &&
+                (rc = check_cuda(cudaMemsetAsync(w->r + 3 * np, 0, sizeof(double) * npseudo, st), "memset")))
+                return rc;
             int it = 0;
             bool all = false;
             if ((rc = pcg(bi, rhs_in, o->maxiter - total_iters, o->use_graph, o->check_every, st, &it, &all))) return rc;

@@ -409,6 +409,84 @@ furax_status deproject_apply(const furax_templates *tp, const void *in, void *ou
     return check_launch("template deprojection (TOD)");
 }
 
+// ------------------------------------------------------------------------------------ augmented
+// The inner FP32 solve of the mixed-precision PCG runs on the augmented normal equations
+//   [P^T W P   P^T W T] [e]   [r]
+//   [T^T W P   T^T W T] [f] = [0],
+// whose map part e solves (P^T F_T P) e = r (eliminate f: f = -G^-1 T^T W P e). Its operator is
+// one fused pass (the amplitudes are one pseudo-pixel per detector that every sample of the
+// detector reads with weights (P_0, P_1, P_2)(tau)), and its block-Jacobi block for a pseudo-
+// pixel is G^-1.
+bool tpl_augmented(const furax_templates *tp, int precision)
+{
+    return tp && precision == FURAX_F32 && tp->order <= 2 && tp->d_aug_ptiles && !long_band(tp->n) &&
+           fused_f32_projects_templates(tp->p);
+}
+
+__global__ void tpl_aug_precond_kernel(int64_t ndet, int64_t base, const double *__restrict__ ginv,
+                                       double *__restrict__ minv, uint8_t *__restrict__ valid)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndet) return;
+    const double *g = ginv + 16 * i;   // zero beyond the order
+    double *m = minv + 6 * (base + i);
+    m[0] = g[0]; m[1] = g[1]; m[2] = g[2]; m[3] = g[5]; m[4] = g[6]; m[5] = g[10];
+    valid[base + i] = 1;
+}
+
+furax_status launch_tpl_aug_precond(const furax_templates *tp, double *minv, uint8_t *valid, cudaStream_t st)
+{
+    if (tp->ndet == 0) return FURAX_OK;
+    tpl_aug_precond_kernel<<<det_grid(tp->ndet), 128, 0, st>>>(tp->ndet, tp->p->npix_total, tp->ginv, minv, valid);
+    count_launches(1);
+    return check_launch("amplitude preconditioner");
+}
+
+// Pixel tiles of the augmented system: every map's pixel tiles, then the amplitude pseudo-pixels
+// of all detectors of its observations; observations carry their map's range.
+static furax_status build_aug_layout(furax_templates *tp, cudaStream_t st)
+{
+    const furax_pointing *p = tp->p;
+    const int64_t base = p->npix_total;
+    std::vector<PTile> pt;
+    std::vector<ObsInfo> ob = p->obs;
+    std::vector<int> owner(p->obs.size());
+    for (size_t i = 0; i < p->obs.size(); ++i) {
+        owner[i] = (int)i;
+        for (size_t j = 0; j < i; ++j)
+            if (p->obs[j].map_off == p->obs[i].map_off) { owner[i] = (int)j; break; }
+    }
+    for (size_t k = 0; k < p->obs.size(); ++k) {
+        if (owner[k] != (int)k) continue;
+        const int64_t first = (int64_t)pt.size();
+        for (int64_t t = 0; t < p->obs[k].nptile; ++t) pt.push_back(p->ptiles[p->obs[k].ptile0 + t]);
+        for (size_t i = k; i < p->obs.size(); ++i) {
+            if (owner[i] != (int)k) continue;
+            for (int32_t d0 = 0; d0 < p->obs[i].ndet; d0 += PTILE) {
+                PTile t;
+                t.p0 = base + p->obs[i].det_off + d0;
+                t.obs = (int32_t)k;
+                t.len = std::min<int32_t>(PTILE, p->obs[i].ndet - d0);
+                pt.push_back(t);
+            }
+        }
+        for (size_t i = k; i < p->obs.size(); ++i)
+            if (owner[i] == (int)k) { ob[i].ptile0 = first; ob[i].nptile = (int32_t)((int64_t)pt.size() - first); }
+    }
+    tp->n_aug_ptiles = (int64_t)pt.size();
+    furax_status rc = check_cuda(cudaMalloc((void **)&tp->d_aug_ptiles, sizeof(PTile) * std::max<size_t>(1, pt.size())),
+                                 "template workspace");
+    if (!rc) rc = check_cuda(cudaMalloc((void **)&tp->d_aug_obs, sizeof(ObsInfo) * ob.size()), "template workspace");
+    if (!rc && !pt.empty())
+        rc = check_cuda(cudaMemcpyAsync(tp->d_aug_ptiles, pt.data(), sizeof(PTile) * pt.size(), cudaMemcpyHostToDevice, st),
+                        "copy layout");
+    if (!rc)
+        rc = check_cuda(cudaMemcpyAsync(tp->d_aug_obs, ob.data(), sizeof(ObsInfo) * ob.size(), cudaMemcpyHostToDevice, st),
+                        "copy layout");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "copy layout");   // the host vectors go out of scope
+    return rc;
+}
+
 // amp[det][l] (l <= K) = G^-1 (W T)^T (d - P m): the template amplitudes of the map m.
 furax_status tpl_amplitudes(const furax_templates *tp, const void *d, int d_t, const double *m, double *amp,
                             cudaStream_t st)
@@ -452,6 +530,7 @@ void templates_destroy(furax_templates *tp)
 {
     if (!tp) return;
     cudaFree(tp->mom); cudaFree(tp->gram); cudaFree(tp->ginv); cudaFree(tp->a); cudaFree(tp->b); cudaFree(tp->bad);
+    cudaFree(tp->d_aug_ptiles); cudaFree(tp->d_aug_obs);
     delete tp;
 }
 
@@ -497,6 +576,7 @@ furax_status templates_create(const furax_pointing *p, const furax_noise *n, int
     if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "template setup");
     if (!rc && bad)
         rc = set_error(FURAX_EBADINPUT, "T^T W T is not positive definite for detector %llu", bad - 1);
+    if (!rc && order <= 2) rc = build_aug_layout(tp, st);
     if (rc) { templates_destroy(tp); return rc; }
     *out = tp;
     return FURAX_OK;

@@ -45,8 +45,8 @@ furax_status prepare_fused_tma();
 
 // Cached FP32 pointing: persistent TMA-pipelined operator (cache rows must be readable up to the
 // next 16-byte boundary past the last sample).
-// With tpl_a, also accumulates the template projection T^T N^-1 P x per detector into tpl_a[det][4].
+// With ft, also does the template work of ft->mode (projection, or the augmented system).
 furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
-                              float4 *lo, double *a64, cudaStream_t st, double *tpl_a = nullptr);
+                              float4 *lo, double *a64, cudaStream_t st, const FusedTpl *ft = nullptr);
 
 }  // namespace fx

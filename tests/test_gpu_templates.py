@@ -233,3 +233,27 @@ def test_full_size_gram_and_annihilation_sampled(fx, dev, orc):
     z = torch.empty_like(x)
     fx._native.furax_noise_inv_apply(N.handle, x, z)
     assert float(y.abs().max()) < 1e-11 * float(z.abs().max())
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_mixed_deprojected_solve_reaches_the_fp64_solve(fx, dev, order):
+    """The mixed solve (inner FP32 iterations on the augmented system [map; amplitudes] for
+    order <= 2, on the explicit correction for order 3) reaches the FP64 solve of the deprojected
+    system; the two observations share one map."""
+    obs = [synth.Observation(8, synth.satellite_scan(ns, t0=31.0 * i), synth.hex_focal_plane(nd), map_id=1)
+           for i, (nd, ns) in enumerate([(5, 9000), (4, 7000)])]
+    taps = np.tile(synth.inverse_noise_taps(), (9, 1))
+    g = synth.rng(33, order)
+    d = np.concatenate([(synth.one_over_f_noise(o.ndet, o.nsamp, g)
+                         + g.normal(size=(o.ndet, 3)) * 100.0 @ ot.legendre_templates(o.nsamp, 2).T).ravel()
+                        for o in obs])
+    P = fx.Pointing.from_observations(obs, mode="cache_mixed", device=dev)
+    N = fx.Noise.banded(P, taps)
+    T = fx.Templates(P, N, order)
+    dt = torch.as_tensor(d.astype(np.float32), device=dev)
+    x64, v64, i64 = fx.mapmaker_cg(P, N, dt, maxiter=500, tol=1e-10, precision="f64", templates=T)
+    x32, v32, i32 = fx.mapmaker_cg(P, N, dt, maxiter=500, tol=1e-10, precision="f32", templates=T)
+    assert i64.converged and i32.converged and i32.true_rel_res <= 1e-10
+    v = v64.cpu().numpy()
+    assert np.array_equal(v, v32.cpu().numpy())
+    assert rel(demono(x32.cpu().numpy(), v), demono(x64.cpu().numpy(), v)) < 1e-7
