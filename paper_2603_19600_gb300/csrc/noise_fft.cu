@@ -1,5 +1,5 @@
-// N^-1 for long symmetric bands by overlap-save (SymmetricBandToeplitzOperator, Table 2: "direct
-// convolution, FFT, overlap and save"; the operator "central to correlated noise modeling").
+// N^-1 for long symmetric bands by overlap-save (SymmetricBandToeplitzOperator, Table 2, offers a
+// direct, an FFT and an overlap-save evaluation; the paper uses the operator for correlated noise).
 //
 // y_t = sum_{k=-H}^{H} c_|k| x_{t+k} over 0 <= t+k < ns (the same finite section as the direct
 // band) is computed block by block: a block of L = 8192 input samples [s - H, s - H + L) (zeros
@@ -9,10 +9,11 @@
 // x1 + i x2 carries two blocks of one detector at once (real part: first block, imaginary part:
 // second block).
 //
-// The transform: one CTA per pair of blocks, L complex values in shared memory, radix-2 stages
-// with a synchronisation between stages; the forward pass is decimation in frequency (natural
-// order in, bit-reversed order out), the spectrum is stored in that bit-reversed order, and the
-// inverse pass is decimation in time (bit-reversed in, natural out), so no permutation is done.
+// The transform: one CTA per pair of blocks, L complex values in shared memory, radix-4 passes
+// (two radix-2 stages each) with a synchronisation between passes; the forward transform is
+// decimation in frequency (natural order in, bit-reversed order out), the spectrum is stored in
+// that bit-reversed order, and the inverse is decimation in time (bit-reversed in, natural out),
+// so no permutation is done.
 #include "tile.cuh"
 
 namespace fx {
@@ -32,42 +33,88 @@ __device__ __forceinline__ T2 cmul(T2 a, T2 b)
     return T2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-// Forward transform (exp(-2 pi i jk/L)), natural order in, bit-reversed order out.
+// (-i) z and (+i) z
+template <typename T2>
+__device__ __forceinline__ T2 mul_neg_i(T2 z) { return T2{z.y, -z.x}; }
+template <typename T2>
+__device__ __forceinline__ T2 mul_pos_i(T2 z) { return T2{-z.y, z.x}; }
+
+// Two consecutive decimation-in-frequency radix-2 stages (spans h = 2^lh, then h/2) fused into one
+// pass of 4-point butterflies on z[i], z[i + h/2], z[i + h], z[i + 3h/2].
+template <typename T2>
+__device__ __forceinline__ void dif_radix4(T2 *z, const T2 *__restrict__ tw, int lh)
+{
+    const int hh = 1 << (lh - 1);
+    const int sh = kFftLog - 1 - lh;   // W_2h^p = tw[p << sh], W_h^p = tw[p << (sh + 1)]
+    for (int g = threadIdx.x; g < kFftL / 4; g += kFftThreads) {
+        const int pos = g & (hh - 1);
+        const int i = ((g >> (lh - 1)) << (lh + 1)) + pos;
+        const T2 a0 = z[i], a1 = z[i + hh], a2 = z[i + 2 * hh], a3 = z[i + 3 * hh];
+        const T2 w1 = tw[pos << sh], w2 = tw[pos << (sh + 1)];
+        const T2 b0 = T2{a0.x + a2.x, a0.y + a2.y}, b1 = T2{a1.x + a3.x, a1.y + a3.y};
+        const T2 c0 = cmul(T2{a0.x - a2.x, a0.y - a2.y}, w1);
+        const T2 c1 = mul_neg_i(cmul(T2{a1.x - a3.x, a1.y - a3.y}, w1));
+        z[i] = T2{b0.x + b1.x, b0.y + b1.y};
+        z[i + hh] = cmul(T2{b0.x - b1.x, b0.y - b1.y}, w2);
+        z[i + 2 * hh] = T2{c0.x + c1.x, c0.y + c1.y};
+        z[i + 3 * hh] = cmul(T2{c0.x - c1.x, c0.y - c1.y}, w2);
+    }
+    __syncthreads();
+}
+
+// Two consecutive decimation-in-time radix-2 stages of the inverse (spans h/2, then h = 2^lh).
+template <typename T2>
+__device__ __forceinline__ void dit_radix4_inv(T2 *z, const T2 *__restrict__ tw, int lh)
+{
+    const int hh = 1 << (lh - 1);
+    const int sh = kFftLog - 1 - lh;
+    for (int g = threadIdx.x; g < kFftL / 4; g += kFftThreads) {
+        const int pos = g & (hh - 1);
+        const int i = ((g >> (lh - 1)) << (lh + 1)) + pos;
+        const T2 a0 = z[i], a1 = z[i + hh], a2 = z[i + 2 * hh], a3 = z[i + 3 * hh];
+        T2 w1 = tw[pos << sh], w2 = tw[pos << (sh + 1)];
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        T2 v = cmul(a1, w2);
+        const T2 b0 = T2{a0.x + v.x, a0.y + v.y}, b1 = T2{a0.x - v.x, a0.y - v.y};
+        v = cmul(a3, w2);
+        const T2 b2 = T2{a2.x + v.x, a2.y + v.y}, b3 = T2{a2.x - v.x, a2.y - v.y};
+        v = cmul(b2, w1);
+        z[i] = T2{b0.x + v.x, b0.y + v.y};
+        z[i + 2 * hh] = T2{b0.x - v.x, b0.y - v.y};
+        v = mul_pos_i(cmul(b3, w1));
+        z[i + hh] = T2{b1.x + v.x, b1.y + v.y};
+        z[i + 3 * hh] = T2{b1.x - v.x, b1.y - v.y};
+    }
+    __syncthreads();
+}
+
+// Forward transform (exp(-2 pi i jk/L)), natural order in, bit-reversed order out: six radix-4
+// passes (spans 4096 and 2048, ..., 4 and 2), then the radix-2 stage of span 1.
 template <typename T2>
 __device__ __forceinline__ void fft_forward_dif(T2 *z, const T2 *__restrict__ tw)
 {
-    for (int s = 0; s < kFftLog; ++s) {
-        const int lh = kFftLog - 1 - s;   // log2 of the butterfly span
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {
-            const int pos = b & (half - 1);
-            const int i = ((b >> lh) << (lh + 1)) + pos;
-            const T2 u = z[i], v = z[i + half];
-            z[i] = T2{u.x + v.x, u.y + v.y};
-            z[i + half] = cmul(T2{u.x - v.x, u.y - v.y}, tw[pos << s]);
-        }
-        __syncthreads();
+    static_assert(kFftLog == 13, "pass schedule written for L = 8192");
+    for (int lh = kFftLog - 1; lh >= 2; lh -= 2) dif_radix4(z, tw, lh);
+    for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {   // span 1: pairs (2b, 2b + 1)
+        const T2 u = z[2 * b], v = z[2 * b + 1];
+        z[2 * b] = T2{u.x + v.x, u.y + v.y};
+        z[2 * b + 1] = T2{u.x - v.x, u.y - v.y};
     }
+    __syncthreads();
 }
 
 // Inverse transform without the 1/L (exp(+2 pi i jk/L)), bit-reversed order in, natural out.
 template <typename T2>
 __device__ __forceinline__ void fft_inverse_dit(T2 *z, const T2 *__restrict__ tw)
 {
-    for (int s = kFftLog - 1; s >= 0; --s) {
-        const int lh = kFftLog - 1 - s;
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {
-            const int pos = b & (half - 1);
-            const int i = ((b >> lh) << (lh + 1)) + pos;
-            T2 w = tw[pos << s];
-            w.y = -w.y;
-            const T2 u = z[i], v = cmul(z[i + half], w);
-            z[i] = T2{u.x + v.x, u.y + v.y};
-            z[i + half] = T2{u.x - v.x, u.y - v.y};
-        }
-        __syncthreads();
+    for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {   // span 1
+        const T2 u = z[2 * b], v = z[2 * b + 1];
+        z[2 * b] = T2{u.x + v.x, u.y + v.y};
+        z[2 * b + 1] = T2{u.x - v.x, u.y - v.y};
     }
+    __syncthreads();
+    for (int lh = 2; lh <= kFftLog - 1; lh += 2) dit_radix4_inv(z, tw, lh);
 }
 
 // tw[m] = exp(-2 pi i m / L), m < L/2.

@@ -1,5 +1,5 @@
-"""Long symmetric bands (65..2048 taps): N^-1 by overlap-save (SymmetricBandToeplitzOperator,
-"direct convolution, FFT, overlap and save", Table 2) and the map-making operators built on it,
+"""Long symmetric bands (65..2048 taps): N^-1 by overlap-save (SymmetricBandToeplitzOperator of
+Table 2, one of whose evaluations is overlap-save) and the map-making operators built on it,
 against the oracle's direct sum."""
 import numpy as np
 import pytest

@@ -1,6 +1,6 @@
-"""Pins for the oracle's symmetric band N^-1 at the long lengths of the FFT / overlap-save method
-(SymmetricBandToeplitzOperator: "direct convolution, FFT, overlap and save", Table 2): the
-oracle keeps the direct sum, checked here against dense Toeplitz matrices and numpy FFTs."""
+"""Pins for the oracle's symmetric band N^-1 at the long lengths of the overlap-save evaluation
+(SymmetricBandToeplitzOperator, Table 2): the oracle keeps the direct sum, checked here against
+dense Toeplitz matrices and numpy FFTs."""
 import numpy as np
 import pytest
 import scipy.linalg
