@@ -546,10 +546,10 @@ def main():
         print(json.dumps({"deproject_only": True, **wl, **r}), flush=True)
         return
 
-    def step():
+    def step(d_ready=None):
         P.refresh()
         return fx.mapmaker_cg(P, N, d, maxiter=CG_ITERS, tol=0.0, precision="f32", acc="f32", inner_tol=0.0,
-                              max_outer=1, true_residual=False, check_every=10)
+                              max_outer=1, true_residual=False, check_every=10, d_ready=d_ready)
 
     # ---------------- warm-up
     with torch.cuda.stream(stream):
@@ -626,13 +626,20 @@ def main():
         torch.cuda.synchronize(dev)
         e2 = torch.cuda.Event(enable_timing=True)
         e3 = torch.cuda.Event(enable_timing=True)
+        # the TOD goes up on a copy stream while the pointing is expanded and the preconditioner
+        # built; the solver waits for it only where it first reads it
+        copy_stream = torch.cuda.Stream(device=dev)
+        d_ready = torch.cuda.Event()
         with torch.cuda.stream(stream):
             e2.record(stream)
             for _ in range(args.steps):
+                copy_stream.wait_stream(stream)   # the previous step has finished reading d
+                with torch.cuda.stream(copy_stream):
+                    d.copy_(d_h, non_blocking=True)
+                    d_ready.record(copy_stream)
                 q_bore.copy_(q_bore_h, non_blocking=True)
                 q_det.copy_(q_det_h, non_blocking=True)
-                d.copy_(d_h, non_blocking=True)
-                x, valid, info = step()
+                x, valid, info = step(d_ready)
                 x_h.copy_(x, non_blocking=True)
             e3.record(stream)
         stream.synchronize()

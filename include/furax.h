@@ -252,6 +252,9 @@ typedef struct {
     int32_t true_residual; /* 1 computes ||b - A64 x||/||b|| at exit (one more application of the
                               FP64 operator); 0 skips it where it is not needed to continue
                               (true_rel_res = -1; FURAX_F32 then stops after its last inner solve) */
+    void *d_ready;         /* cudaEvent_t recorded once d is written (e.g. after its host-to-device
+                              copy on another stream), or NULL: the solver waits for it only before
+                              it reads d, so the copy overlaps the preconditioner set-up */
 } furax_cg_opts;
 
 typedef struct {

@@ -42,7 +42,7 @@ class CgOpts(ctypes.Structure):
     _fields_ = [("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("acc", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_every", ctypes.c_int32), ("rcond_min", ctypes.c_double),
-                ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32)]
+                ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32), ("d_ready", ctypes.c_void_p)]
 
 
 class CgResult(ctypes.Structure):

@@ -631,6 +631,7 @@ void furax_cg_default_opts(furax_cg_opts *o)
     o->rcond_min = 1e-3;
     o->binned_only = 0;
     o->true_residual = 1;
+    o->d_ready = nullptr;
 }
 
 furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t, double *x,

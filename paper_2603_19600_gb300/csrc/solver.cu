@@ -768,7 +768,9 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
 
     // Preconditioner and mask (FP64 blocks from the handle's pointing).
     if ((rc = launch_bj(p, n, o->rcond_min, w->minv, w->valid, nullptr, nullptr, st))) return rc;
-    // Right-hand side b = S P^T N^-1 d in FP64.
+    // Right-hand side b = S P^T N^-1 d in FP64 (the first read of d).
+    if (o->d_ready && (rc = check_cuda(cudaStreamWaitEvent(st, (cudaEvent_t)o->d_ready, 0), "wait for d")))
+        return rc;
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
     if (long_band(n)) {
         // TOD workspaces exist before any stream capture of the iteration

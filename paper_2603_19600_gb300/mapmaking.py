@@ -255,15 +255,19 @@ class SolveInfo:
 
 def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64", acc="f32", inner_tol=1e-5,
                 max_outer=8, use_graph=True, check_every=10, rcond_min=1e-3, binned_only=False, hist_len=None,
-                out=None, true_residual=True, templates: "Templates | None" = None, amplitudes=None):
+                out=None, true_residual=True, templates: "Templates | None" = None, amplitudes=None,
+                d_ready=None):
     """Solve the map-making normal equations per observation; returns (map, valid mask, SolveInfo).
     With ``templates`` the system is the deprojected one (P^T F_T P) x = P^T F_T d; ``amplitudes``
-    (float64 [ndet_total][order+1], optional) then receives the template amplitudes of the map."""
+    (float64 [ndet_total][order+1], optional) then receives the template amplitudes of the map.
+    ``d_ready`` (a torch.cuda.Event recorded once d is written) lets the solver start its
+    preconditioner before d has arrived."""
     o = nat.default_cg_opts()
     o.maxiter, o.tol, o.precision, o.acc = int(maxiter), float(tol), _PREC[precision], _ACC[acc]
     o.inner_tol, o.max_outer, o.use_graph = float(inner_tol), int(max_outer), int(bool(use_graph))
     o.check_every, o.rcond_min, o.binned_only = int(check_every), float(rcond_min), int(bool(binned_only))
     o.true_residual = int(bool(true_residual))
+    o.d_ready = None if d_ready is None else d_ready.cuda_event
     x = out if out is not None else torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device)
     valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
     hl = hist_len if hist_len is not None else maxiter + 1

@@ -193,3 +193,23 @@ def test_pcg_converges_with_precession_repeats(fx, dev, orc):
     assert im.converged and im.true_rel_res <= 1e-8
     assert rel(x64.cpu().numpy()[v], ox[v]) < 1e-6
     assert rel(xm.cpu().numpy()[v], ox[v]) < 1e-6
+
+
+def test_d_ready_event_orders_the_tod_upload(fx, dev):
+    """d copied from pinned host memory on another stream, with its event passed as d_ready, gives
+    the solve of the same data already on the device (the solver waits only where it reads d)."""
+    o = synth.Observation(16, synth.satellite_scan(20000, t0=9.0), synth.hex_focal_plane(8))
+    P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    N = fx.Noise.banded(P, np.tile(synth.inverse_noise_taps(), (8, 1)))
+    d_h = torch.randn(P.nsamp_total, generator=torch.Generator().manual_seed(3)).pin_memory()
+    xr, vr, _ = fx.mapmaker_cg(P, N, d_h.to(dev), maxiter=30, tol=0.0, precision="f64")
+    d = torch.zeros(P.nsamp_total, device=dev)
+    torch.cuda.synchronize()
+    cs = torch.cuda.Stream(device=dev)
+    ev = torch.cuda.Event()
+    with torch.cuda.stream(cs):
+        d.copy_(d_h, non_blocking=True)
+        ev.record(cs)
+    x, v, _ = fx.mapmaker_cg(P, N, d, maxiter=30, tol=0.0, precision="f64", d_ready=ev)
+    assert torch.equal(v, vr)
+    assert (torch.linalg.norm(x - xr) / torch.linalg.norm(xr)).item() < 1e-12
