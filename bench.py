@@ -51,6 +51,8 @@ def parse():
                     help="skip the batched, precision-sweep and gradient measurements")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the fused P^T N^-1 P apply (profiling runs; not a bench line)")
+    ap.add_argument("--long-band-only", action="store_true",
+                    help="time only the 1024-tap overlap-save N^-1 and its normal operator (profiling runs)")
     ap.add_argument("--deproject-only", action="store_true",
                     help="time only the template-deprojected solver step (profiling runs; not a bench line)")
     ap.add_argument("--ndet", type=int, default=None, help="override the detector count (profiling runs)")
@@ -539,6 +541,11 @@ def main():
         ms, n = nat.furax_profile_read(0)
         print(json.dumps({"apply_only": True, **wl, "acc": args.acc, "ms_per_apply": ms / max(n, 1),
                           "gsamples_per_s": S / (ms / max(n, 1) / 1e3) / 1e9, "launches": n}), flush=True)
+        return
+
+    if args.long_band_only:
+        r = long_band(fx, dev, stream, wl, q_bore, q_det, reps=max(1, args.steps))
+        print(json.dumps({"long_band_only": True, **wl, **r}), flush=True)
         return
 
     if args.deproject_only:
