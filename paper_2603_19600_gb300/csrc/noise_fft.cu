@@ -9,11 +9,12 @@
 // x1 + i x2 carries two blocks of one detector at once (real part: first block, imaginary part:
 // second block).
 //
-// The transform: one CTA per pair of blocks, L complex values in shared memory, radix-4 passes
-// (two radix-2 stages each) with a synchronisation between passes; the forward transform is
-// decimation in frequency (natural order in, bit-reversed order out), the spectrum is stored in
-// that bit-reversed order, and the inverse is decimation in time (bit-reversed in, natural out),
-// so no permutation is done.
+// The transform: one CTA per pair of blocks, L complex values in shared memory. Spans of 32 and
+// more go in radix-4 passes (two radix-2 stages each, a synchronisation between passes); the
+// spans below 32, whose shared-memory patterns conflict, run in registers with one warp per 32
+// consecutive values. The forward transform is decimation in frequency (natural order in,
+// bit-reversed order out), the spectrum is stored in that bit-reversed order, and the inverse is
+// decimation in time (bit-reversed in, natural out), so no permutation is done.
 #include "tile.cuh"
 
 namespace fx {
@@ -39,13 +40,16 @@ __device__ __forceinline__ T2 mul_neg_i(T2 z) { return T2{z.y, -z.x}; }
 template <typename T2>
 __device__ __forceinline__ T2 mul_pos_i(T2 z) { return T2{-z.y, z.x}; }
 
-// Two consecutive decimation-in-frequency radix-2 stages (spans h = 2^lh, then h/2) fused into one
-// pass of 4-point butterflies on z[i], z[i + h/2], z[i + h], z[i + 3h/2].
-template <typename T2>
-__device__ __forceinline__ void dif_radix4(T2 *z, const T2 *__restrict__ tw, int lh)
+// Two consecutive decimation-in-frequency radix-2 stages (spans h = 2^LH, then h/2) fused into one
+// pass of 4-point butterflies on z[i], z[i + h/2], z[i + h], z[i + 3h/2]. LH is a compile-time
+// constant so that, for spans of 1024 and less, a thread's butterflies share their twiddles.
+template <int LH, typename T2>
+__device__ __forceinline__ void dif_radix4(T2 *z, const T2 *__restrict__ tw)
 {
-    const int hh = 1 << (lh - 1);
-    const int sh = kFftLog - 1 - lh;   // W_2h^p = tw[p << sh], W_h^p = tw[p << (sh + 1)]
+    constexpr int lh = LH;
+    constexpr int hh = 1 << (lh - 1);
+    constexpr int sh = kFftLog - 1 - lh;   // W_2h^p = tw[p << sh], W_h^p = tw[p << (sh + 1)]
+#pragma unroll
     for (int g = threadIdx.x; g < kFftL / 4; g += kFftThreads) {
         const int pos = g & (hh - 1);
         const int i = ((g >> (lh - 1)) << (lh + 1)) + pos;
@@ -62,12 +66,14 @@ __device__ __forceinline__ void dif_radix4(T2 *z, const T2 *__restrict__ tw, int
     __syncthreads();
 }
 
-// Two consecutive decimation-in-time radix-2 stages of the inverse (spans h/2, then h = 2^lh).
-template <typename T2>
-__device__ __forceinline__ void dit_radix4_inv(T2 *z, const T2 *__restrict__ tw, int lh)
+// Two consecutive decimation-in-time radix-2 stages of the inverse (spans h/2, then h = 2^LH).
+template <int LH, typename T2>
+__device__ __forceinline__ void dit_radix4_inv(T2 *z, const T2 *__restrict__ tw)
 {
-    const int hh = 1 << (lh - 1);
-    const int sh = kFftLog - 1 - lh;
+    constexpr int lh = LH;
+    constexpr int hh = 1 << (lh - 1);
+    constexpr int sh = kFftLog - 1 - lh;
+#pragma unroll
     for (int g = threadIdx.x; g < kFftL / 4; g += kFftThreads) {
         const int pos = g & (hh - 1);
         const int i = ((g >> (lh - 1)) << (lh + 1)) + pos;
@@ -95,7 +101,12 @@ template <typename T2>
 __device__ __forceinline__ void fft_forward_dif(T2 *z, const T2 *__restrict__ tw)
 {
     static_assert(kFftLog == 13, "pass schedule written for L = 8192");
-    for (int lh = kFftLog - 1; lh >= 2; lh -= 2) dif_radix4(z, tw, lh);
+    dif_radix4<12>(z, tw);
+    dif_radix4<10>(z, tw);
+    dif_radix4<8>(z, tw);
+    dif_radix4<6>(z, tw);
+    dif_radix4<4>(z, tw);
+    dif_radix4<2>(z, tw);
     for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {   // span 1: pairs (2b, 2b + 1)
         const T2 u = z[2 * b], v = z[2 * b + 1];
         z[2 * b] = T2{u.x + v.x, u.y + v.y};
@@ -104,17 +115,49 @@ __device__ __forceinline__ void fft_forward_dif(T2 *z, const T2 *__restrict__ tw
     __syncthreads();
 }
 
-// Inverse transform without the 1/L (exp(+2 pi i jk/L)), bit-reversed order in, natural out.
 template <typename T2>
-__device__ __forceinline__ void fft_inverse_dit(T2 *z, const T2 *__restrict__ tw)
+__device__ __forceinline__ T2 shfl_xor2(T2 v, int m)
 {
-    for (int b = threadIdx.x; b < kFftL / 2; b += kFftThreads) {   // span 1
-        const T2 u = z[2 * b], v = z[2 * b + 1];
-        z[2 * b] = T2{u.x + v.x, u.y + v.y};
-        z[2 * b + 1] = T2{u.x - v.x, u.y - v.y};
+    return T2{__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
+
+// Spans 16 .. 1 of the forward transform, the spectrum multiply and spans 1 .. 16 of the inverse,
+// on 32 consecutive values held one per lane (butterfly partners by xor shuffles): the stages
+// whose shared-memory access patterns conflict, done without shared memory.
+template <typename T, typename T2>
+__device__ __forceinline__ void fft_tail_in_warps(T2 *z, const T2 *__restrict__ tw, const T *__restrict__ sp)
+{
+    const int lane = threadIdx.x & 31;
+    T2 w[5];   // this lane's twiddle at spans 1, 2, 4, 8, 16 (the same for every block)
+#pragma unroll
+    for (int ls = 0; ls <= 4; ++ls) w[ls] = tw[(lane & ((1 << ls) - 1)) << (kFftLog - 1 - ls)];
+    for (int base = threadIdx.x & ~31; base < kFftL; base += kFftThreads) {
+        T2 x = z[base + lane];
+#pragma unroll
+        for (int ls = 4; ls >= 0; --ls) {
+            const int s = 1 << ls;
+            const T2 p = shfl_xor2(x, s);
+            x = (lane & s) ? cmul(T2{p.x - x.x, p.y - x.y}, w[ls]) : T2{x.x + p.x, x.y + p.y};
+        }
+        const T f = sp[base + lane];
+        x.x *= f;
+        x.y *= f;
+#pragma unroll
+        for (int ls = 0; ls <= 4; ++ls) {
+            const int s = 1 << ls;
+            const T2 p = shfl_xor2(x, s);
+            const T2 wc = T2{w[ls].x, -w[ls].y};
+            if (lane & s) {
+                const T2 t = cmul(x, wc);
+                x = T2{p.x - t.x, p.y - t.y};
+            } else {
+                const T2 t = cmul(p, wc);
+                x = T2{x.x + t.x, x.y + t.y};
+            }
+        }
+        z[base + lane] = x;
     }
     __syncthreads();
-    for (int lh = 2; lh <= kFftLog - 1; lh += 2) dit_radix4_inv(z, tw, lh);
 }
 
 // tw[m] = exp(-2 pi i m / L), m < L/2.
@@ -176,15 +219,17 @@ __global__ void __launch_bounds__(kFftThreads) ninv_fft_kernel(const FftItem *__
         z[j] = T2{re, im};
     }
     __syncthreads();
-    fft_forward_dif<T2>(z, tw);
-    const T *sp = spec + gdet * kFftL;
-    for (int j = threadIdx.x; j < kFftL; j += kFftThreads) {
-        const T f = sp[j];
-        z[j].x *= f;
-        z[j].y *= f;
-    }
-    __syncthreads();
-    fft_inverse_dit<T2>(z, tw);
+    // forward spans 4096 .. 32 (radix-4 passes), then spans 16 .. 1, the spectrum and the inverse
+    // spans 1 .. 16 in registers, then the inverse spans 32 .. 4096
+    dif_radix4<12>(z, tw);
+    dif_radix4<10>(z, tw);
+    dif_radix4<8>(z, tw);
+    dif_radix4<6>(z, tw);
+    fft_tail_in_warps<T, T2>(z, tw, spec + gdet * kFftL);
+    dit_radix4_inv<6>(z, tw);
+    dit_radix4_inv<8>(z, tw);
+    dit_radix4_inv<10>(z, tw);
+    dit_radix4_inv<12>(z, tw);
     const T scale = T(1) / T(kFftL);
     DT *orow = out + ob.tod_off + (int64_t)it.det * ns;
     for (int j = threadIdx.x; j < m; j += kFftThreads) {
