@@ -154,6 +154,33 @@ def inverse_noise_taps(ntaps: int = NTAPS, fsamp: float = FSAMP_HZ, sigma: float
     return c * (1.0 - np.arange(ntaps) / ntaps)
 
 
+def noise_covariance_band(ntaps: int = NTAPS, fsamp: float = FSAMP_HZ, sigma: float = SIGMA_UK,
+                          fknee: float = FKNEE_HZ, alpha: float = ALPHA, fmin: float = 0.01,
+                          nfft: int = 1 << 16) -> np.ndarray:
+    """Band of a stationary noise covariance, lags 0..ntaps-1 (uK^2): the autocovariance of the
+    1/f + white spectrum with the 1/f part cut off below fmin (PSD sigma^2 (1 + (fknee /
+    sqrt(f^2 + fmin^2))^alpha)), Bartlett-tapered so that every finite section is positive definite."""
+    f = np.fft.rfftfreq(nfft, d=1.0 / fsamp)
+    psd = sigma ** 2 * (1.0 + (fknee / np.sqrt(f ** 2 + fmin ** 2)) ** alpha)
+    c = np.fft.irfft(psd, n=nfft)[:ntaps]
+    return c * (1.0 - np.arange(ntaps) / ntaps)
+
+
+def band_realization(taps: np.ndarray, nsamp: int, g: np.random.Generator) -> np.ndarray:
+    """Gaussian streams [ndet][nsamp] whose covariance is the symmetric band taps [ndet][K]
+    (circulant embedding: white noise shaped by the square root of the band's non-negative
+    spectrum on a periodic grid longer than nsamp + 2K)."""
+    taps = np.atleast_2d(np.asarray(taps, np.float64))
+    ndet, k = taps.shape
+    n = 1 << int(np.ceil(np.log2(nsamp + 2 * k)))
+    kern = np.zeros((ndet, n))
+    kern[:, :k] = taps
+    kern[:, n - k + 1:] = taps[:, 1:][:, ::-1]
+    spec = np.maximum(np.fft.rfft(kern, axis=1).real, 0.0)
+    w = g.normal(size=(ndet, n))
+    return np.fft.irfft(np.fft.rfft(w, axis=1) * np.sqrt(spec), n=n, axis=1)[:, :nsamp]
+
+
 def white_noise(ndet: int, nsamp: int, g: np.random.Generator, sigma: float = SIGMA_UK) -> np.ndarray:
     return g.normal(0.0, sigma, (ndet, nsamp))
 
