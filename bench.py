@@ -361,6 +361,39 @@ def long_band(fx, dev, stream, wl, q_bore, q_det, ntaps: int = 1024, reps: int =
     return out
 
 
+def gap_fill(fx, dev, stream, wl, q_bore, q_det, d, reps: int = 2):
+    """Gap filling by constrained realisation on the same 256 x 2^20 TOD: about 10 % of the samples
+    in gaps (random ones and 2000-sample stretches every 100000 samples), 64-tap covariance band,
+    zero realisation (the filled values are then the conditional mean), CG per detector to 1e-8."""
+    import torch
+    nside, nd, ns = wl["nside"], wl["ndet"], wl["nsamp"]
+    S = nd * ns
+    with torch.cuda.stream(stream):
+        P = fx.Pointing(q_bore, q_det, [nd], [ns], [nside], mode="cache_f32", stream=stream)
+        C = fx.Noise.banded(P, np.tile(synth.noise_covariance_band(64), (nd, 1)))
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 707)
+        valid = torch.rand(nd, ns, generator=g, device=dev) > 0.08
+        for start in range(5000, ns, 100000):
+            valid[:, start:start + 2000] = False
+        valid = valid.reshape(-1).to(torch.uint8)
+        zero = torch.zeros_like(d)
+        out = torch.empty_like(d)
+        _, iters, ok = fx.gapfill(C, d, valid, zero, maxiter=500, tol=1e-8, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fx.gapfill(C, d, valid, zero, maxiter=500, tol=1e-8, out=out)
+        e1.record(stream)
+        stream.synchronize()
+        gaps = int(S - int(valid.sum()))
+        P.close()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "same TOD, ~10 % of samples in gaps, 64-tap covariance band, conditional mean, CG to 1e-8",
+            "ms": ms, "gap_samples": gaps, "iterations_max": int(max(iters)), "converged": bool(ok),
+            "gsamples_per_s": S / (ms / 1e3) / 1e9}
+
+
 def batched_c4(fx, dev, stream, steps: int, joint: bool = False):
     """The batched configuration: 64 independent observations, lengths uniform in [2^18, 2^22],
     8-128 detectors, nside 256/512 alternating (9.75 G samples), one launch per operator over the
@@ -660,7 +693,8 @@ def main():
         out["hwp"] = hwp_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps=max(1, min(args.steps, 3)))
     # ---------------- the other configurations of the workload: batched, precision, gradients
     if rank == 0 and world == 1 and not args.no_extra and not args.small:
-        for key, fn in (("long_band", lambda: long_band(fx, dev, stream, wl, q_bore, q_det)),
+        for key, fn in (("gap_fill", lambda: gap_fill(fx, dev, stream, wl, q_bore, q_det, d)),
+                        ("long_band", lambda: long_band(fx, dev, stream, wl, q_bore, q_det)),
                         ("deproject", lambda: deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps,
                                                               steps=max(1, min(args.steps, 3)))),
                         ("precision_sweep", lambda: precision_sweep(fx, dev, stream)),

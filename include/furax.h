@@ -321,6 +321,25 @@ furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void 
                                          double *amplitudes, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Gap filling by constrained Gaussian realisation (the use the paper gives the symmetric band
+ * Toeplitz operator besides noise weighting; SymmetricBandToeplitzOperator, Table 2). The paper
+ * does not state the construction; this is the standard conditional one: with N the noise
+ * covariance, v the observed samples, g the gaps and n a realisation of covariance N,
+ *   d_g <- n_g + N_gv N_vv^-1 (d_v - n_v),   d_v unchanged,
+ * with N_vv^-1 applied by conjugate gradients for every detector at once.
+ * ------------------------------------------------------------------------------------- */
+
+/* cov: a banded noise handle whose taps hold the covariance band N (lags 0..ntaps-1, up to
+ * 2048; bands above 64 taps use the overlap-save product). d, n_real, out: device
+ * [nsamp_total] of dtype (out may be d); valid: device uint8 [nsamp_total], 1 = observed. n_real
+ * is the unconstrained realisation (the caller's random draws). Per detector, CG from 0 until
+ * ||r|| <= tol ||r_0|| or maxiter iterations; iters_out: host int32 [sum ndet] or NULL.
+ * Allocates 4 FP64 TOD workspaces for the call and synchronises stream. FURAX_ENOTCONVERGED
+ * when a detector stopped at maxiter (out is still written). */
+furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,
+                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t *iters_out, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * chi^2 and its gradients (differentiability, "Summary"; "Research Impact Statement").
  * ------------------------------------------------------------------------------------- */
 

@@ -653,6 +653,19 @@ furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n
     return mapmaker_cg(p, n, d, d_t, x, valid, o, res, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------- gap filling
+furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,
+                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t *iters_out, void *stream)
+{
+    REQUIRE(cov, "covariance handle is NULL");
+    REQUIRE(cov->kind == FURAX_NOISE_BANDED, "the covariance must be a banded noise handle");
+    REQUIRE(d && valid && n_real && out, "d, valid, n_real and out must be device pointers");
+    REQUIRE(valid_dtype(dtype), "unknown dtype %d", dtype);
+    REQUIRE(maxiter >= 0 && maxiter <= 1000000, "maxiter out of range");
+    REQUIRE(tol >= 0.0, "tol must be >= 0");
+    return gapfill(cov, d, valid, n_real, out, dtype, maxiter, tol, iters_out, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------- templates
 furax_status furax_templates_create(const furax_pointing_t *p, const furax_noise_t *n, int32_t order, void *stream,
                                     furax_templates_t **out)

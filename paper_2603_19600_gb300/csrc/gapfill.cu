@@ -1,0 +1,237 @@
+// Gap filling by constrained Gaussian realisation, the use the Furax paper gives its symmetric
+// band Toeplitz operator besides noise weighting (SymmetricBandToeplitzOperator, Table 2). With N
+// the noise covariance (a symmetric band per detector), d the data, v the observed samples, g the
+// gaps and n an unconstrained realisation of covariance N (supplied by the caller: the random
+// draws of the method),
+//     d_g <- n_g + N_gv N_vv^-1 (d_v - n_v),    d_v unchanged.
+// N_vv^-1 is applied by conjugate gradients run for every detector at once: the operator is the
+// band product (direct, or overlap-save for long bands) between two applications of the mask,
+// and each detector keeps its own scalars (per-CTA partial sums reduced into them).
+#include "tile.cuh"
+
+namespace fx {
+
+struct GfDet {
+    double rr, rr0, pq, rr_new, alpha, beta;
+    int32_t done, iters;
+};
+
+__device__ __forceinline__ double cta_sum_d(double v)
+{
+    __shared__ double red[FT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < FT / 32; ++w) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ int64_t tod_index(const ObsInfo &ob, const Tile &tl, int u)
+{
+    return ob.tod_off + (int64_t)tl.det * ob.nsamp + tl.t0 + u;
+}
+
+// r = S (d - n), p = r, y = 0; rr[det] += |r|^2.
+template <typename DT>
+__global__ void __launch_bounds__(FT) gf_init_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                     const DT *__restrict__ d, const DT *__restrict__ nr,
+                                                     const uint8_t *__restrict__ valid, double *__restrict__ y,
+                                                     double *__restrict__ r, double *__restrict__ p,
+                                                     GfDet *__restrict__ sc)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    double acc = 0.0;
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        const double rv = valid[i] ? (double)d[i] - (double)nr[i] : 0.0;
+        r[i] = rv;
+        p[i] = rv;
+        y[i] = 0.0;
+        acc += rv * rv;
+    }
+    acc = cta_sum_d(acc);
+    if (threadIdx.x == 0) red_add_f64(&sc[ob.det_off + tl.det].rr, acc);
+}
+
+__global__ void gf_start_kernel(int64_t ndet, GfDet *__restrict__ sc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndet) return;
+    GfDet &s = sc[i];
+    s.rr0 = s.rr;
+    s.done = s.rr0 > 0.0 ? 0 : 1;
+    s.iters = 0;
+    s.pq = 0.0;
+    s.rr_new = 0.0;
+}
+
+// q = S q (masked band product of p); pq[det] += p . q.
+__global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                   const uint8_t *__restrict__ valid, const double *__restrict__ p,
+                                                   double *__restrict__ q, GfDet *__restrict__ sc)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    if (sc[ob.det_off + tl.det].done) return;
+    double acc = 0.0;
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        const double qv = valid[i] ? q[i] : 0.0;
+        q[i] = qv;
+        acc += p[i] * qv;
+    }
+    acc = cta_sum_d(acc);
+    if (threadIdx.x == 0) red_add_f64(&sc[ob.det_off + tl.det].pq, acc);
+}
+
+__global__ void gf_alpha_kernel(int64_t ndet, GfDet *__restrict__ sc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndet) return;
+    GfDet &s = sc[i];
+    s.alpha = (!s.done && s.pq > 0.0) ? s.rr / s.pq : 0.0;
+    s.rr_new = 0.0;
+}
+
+// y += alpha p; r -= alpha q; rr_new[det] += |r|^2.
+__global__ void __launch_bounds__(FT) gf_update_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                       const double *__restrict__ p, const double *__restrict__ q,
+                                                       double *__restrict__ y, double *__restrict__ r,
+                                                       GfDet *__restrict__ sc)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const GfDet s = sc[ob.det_off + tl.det];
+    if (s.done) return;
+    double acc = 0.0;
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        y[i] += s.alpha * p[i];
+        const double rv = r[i] - s.alpha * q[i];
+        r[i] = rv;
+        acc += rv * rv;
+    }
+    acc = cta_sum_d(acc);
+    if (threadIdx.x == 0) red_add_f64(&sc[ob.det_off + tl.det].rr_new, acc);
+}
+
+__global__ void gf_beta_kernel(int64_t ndet, double tol2, GfDet *__restrict__ sc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndet) return;
+    GfDet &s = sc[i];
+    s.pq = 0.0;
+    if (s.done) { s.beta = 0.0; return; }
+    s.beta = s.rr > 0.0 ? s.rr_new / s.rr : 0.0;
+    s.rr = s.rr_new;
+    s.iters += 1;
+    if (s.rr <= tol2 * s.rr0) s.done = 1;
+}
+
+// p = r + beta p (detectors still iterating).
+__global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                    const double *__restrict__ r, double *__restrict__ p,
+                                                    const GfDet *__restrict__ sc)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const GfDet s = sc[ob.det_off + tl.det];
+    if (s.done) return;
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        p[i] = r[i] + s.beta * p[i];
+    }
+}
+
+// out = d on observed samples, n + (N y) in the gaps.
+template <typename DT>
+__global__ void __launch_bounds__(FT) gf_fill_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                     const DT *__restrict__ d, const DT *__restrict__ nr,
+                                                     const uint8_t *__restrict__ valid, const double *__restrict__ ny,
+                                                     DT *__restrict__ out)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        out[i] = valid[i] ? d[i] : (DT)((double)nr[i] + ny[i]);
+    }
+}
+
+furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, const void *nr, void *out, int dtype,
+                     int maxiter, double tol, int32_t *iters_out, cudaStream_t st)
+{
+    const int64_t ns = n->nsamp_total, nd = n->ndet_total;
+    if (ns == 0 || nd == 0) return FURAX_OK;
+    const unsigned g = (unsigned)n->n_tiles;
+    const unsigned dg = (unsigned)((nd + 127) / 128);
+    double *y = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    GfDet *sc = nullptr;
+    furax_status rc = FURAX_OK;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (!rc) rc = check_cuda(cudaMalloc(ptr, bytes), "gap-filling workspace");
+    };
+    alloc((void **)&y, sizeof(double) * ns);
+    alloc((void **)&r, sizeof(double) * ns);
+    alloc((void **)&p, sizeof(double) * ns);
+    alloc((void **)&q, sizeof(double) * ns);
+    alloc((void **)&sc, sizeof(GfDet) * nd);
+    std::vector<GfDet> h(nd);
+    bool all_done = false;
+    if (!rc) rc = check_cuda(cudaMemsetAsync(sc, 0, sizeof(GfDet) * nd, st), "memset");
+    if (!rc) {
+        if (dtype == FURAX_F64)
+            gf_init_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const double *)d, (const double *)nr, valid,
+                                                      y, r, p, sc);
+        else
+            gf_init_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const float *)d, (const float *)nr, valid,
+                                                     y, r, p, sc);
+        gf_start_kernel<<<dg, 128, 0, st>>>(nd, sc);
+        count_launches(2);
+        rc = check_launch("gap filling (start)");
+    }
+    for (int it = 0; !rc && it < maxiter && !all_done; ++it) {
+        if ((rc = launch_ninv(n, p, q, FURAX_F64, st))) break;   // q = N p
+        gf_pq_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, sc);
+        gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
+        gf_update_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, q, y, r, sc);
+        gf_beta_kernel<<<dg, 128, 0, st>>>(nd, tol * tol, sc);
+        gf_dir_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, r, p, sc);
+        count_launches(5);
+        if ((rc = check_launch("gap filling (iteration)"))) break;
+        if ((it + 1) % 16 == 0 || it + 1 == maxiter) {
+            if ((rc = check_cuda(cudaMemcpyAsync(h.data(), sc, sizeof(GfDet) * nd, cudaMemcpyDeviceToHost, st), "read")))
+                break;
+            if ((rc = check_cuda(cudaStreamSynchronize(st), "gap filling"))) break;
+            all_done = true;
+            for (const GfDet &s : h) all_done = all_done && s.done;
+        }
+    }
+    if (!rc) rc = launch_ninv(n, y, q, FURAX_F64, st);   // q = N y
+    if (!rc) {
+        if (dtype == FURAX_F64)
+            gf_fill_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const double *)d, (const double *)nr, valid,
+                                                      q, (double *)out);
+        else
+            gf_fill_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const float *)d, (const float *)nr, valid,
+                                                     q, (float *)out);
+        count_launches(1);
+        rc = check_launch("gap filling (fill)");
+    }
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(h.data(), sc, sizeof(GfDet) * nd, cudaMemcpyDeviceToHost, st), "read");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "gap filling");
+    cudaFree(y); cudaFree(r); cudaFree(p); cudaFree(q); cudaFree(sc);
+    if (rc) return rc;
+    all_done = true;
+    for (int64_t i = 0; i < nd; ++i) {
+        all_done = all_done && h[i].done;
+        if (iters_out) iters_out[i] = h[i].iters;
+    }
+    return all_done ? FURAX_OK : FURAX_ENOTCONVERGED;
+}
+
+}  // namespace fx

@@ -307,6 +307,9 @@ furax_status tpl_amplitudes(const furax_templates *tp, const void *d, int d_t, c
 // out [ndet][K+1][K+1] = T^T W T.
 furax_status tpl_gram_out(const furax_templates *tp, double *out, cudaStream_t st);
 // out = F_T in for a TOD (in != out).
+// Gap filling by constrained realisation (gapfill.cu); n holds the covariance band.
+furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, const void *nr, void *out, int dtype,
+                     int maxiter, double tol, int32_t *iters_out, cudaStream_t st);
 furax_status deproject_apply(const furax_templates *tp, const void *in, void *out, int dtype, cudaStream_t st);
 
 }  // namespace fx
