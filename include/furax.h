@@ -333,11 +333,14 @@ furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void 
  * 2048; bands above 64 taps use the overlap-save product). d, n_real, out: device
  * [nsamp_total] of dtype (out may be d); valid: device uint8 [nsamp_total], 1 = observed. n_real
  * is the unconstrained realisation (the caller's random draws). Per detector, CG from 0 until
- * ||r|| <= tol ||r_0|| or maxiter iterations; iters_out: host int32 [sum ndet] or NULL.
- * Allocates 4 FP64 TOD workspaces for the call and synchronises stream. FURAX_ENOTCONVERGED
- * when a detector stopped at maxiter (out is still written). */
+ * ||r|| <= tol ||r_0|| or maxiter iterations; precision FURAX_F64 applies N in FP64, FURAX_F32 in
+ * FP32 (vectors and scalars stay FP64; the filled values are then good to ~1e-7 relative);
+ * iters_out: host int32 [sum ndet] or NULL. Allocates 4 FP64 TOD workspaces (+ 2 FP32) for the
+ * call and synchronises stream. FURAX_ENOTCONVERGED when a detector stopped at maxiter (out is
+ * still written). */
 furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,
-                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t *iters_out, void *stream);
+                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t precision,
+                           int32_t *iters_out, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * chi^2 and its gradients (differentiability, "Summary"; "Research Impact Statement").

@@ -74,7 +74,7 @@ _SIGS = {
     "furax_ptnp_apply_noalloc": [_V, _V, _V, _I32, _I64, _I32, _V, _I32, _V, _V, _V, _V],
     "furax_mapmaker_cg": [_V, _V, _V, _I32, _V, _V, ctypes.POINTER(CgOpts), ctypes.POINTER(CgResult), _V],
     "furax_chi2_grad": [_V, _V, _V, _I32, _V, _V, _V, _V, _I32, _V],
-    "furax_gapfill": [_V, _V, _V, _V, _V, _I32, _I32, _D, _V, _V],
+    "furax_gapfill": [_V, _V, _V, _V, _V, _I32, _I32, _D, _I32, _V, _V],
     "furax_templates_create": [_V, _V, _I32, _V, ctypes.POINTER(_V)],
     "furax_templates_destroy": [_V],
     "furax_templates_gram": [_V, _V, _V],
@@ -308,14 +308,14 @@ def furax_mapmaker_cg(hp, hn, d, x, valid=None, opts: CgOpts | None = None, hist
     return rc, res, [hist[i] for i in range(res.hist_written)]
 
 
-def furax_gapfill(hn, ndet, d, valid, n_real, out, maxiter=1000, tol=1e-10, stream=None):
+def furax_gapfill(hn, ndet, d, valid, n_real, out, maxiter=1000, tol=1e-10, precision=FURAX_F64, stream=None):
     """Returns (status, per-detector iterations); ndet = detectors of the handle."""
     if not (d.dtype == n_real.dtype == out.dtype):
         raise ValueError("d, n_real and out must have one dtype")
     iters = (ctypes.c_int32 * max(int(ndet), 1))()
     rc = _call("furax_gapfill", hn, _ptr(d, None, None, "d"), _ptr(valid, torch.uint8, d.numel(), "valid"),
                _ptr(n_real, None, d.numel(), "n_real"), _ptr(out, None, d.numel(), "out"), _dt(d), int(maxiter),
-               float(tol), iters, _stream(stream), ok=(FURAX_OK, FURAX_ENOTCONVERGED))
+               float(tol), int(precision), iters, _stream(stream), ok=(FURAX_OK, FURAX_ENOTCONVERGED))
     return rc, [iters[i] for i in range(ndet)]
 
 

@@ -655,7 +655,8 @@ furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n
 
 // ---------------------------------------------------------------------------- gap filling
 furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,
-                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t *iters_out, void *stream)
+                           void *out, int32_t dtype, int32_t maxiter, double tol, int32_t precision, int32_t *iters_out,
+                           void *stream)
 {
     REQUIRE(cov, "covariance handle is NULL");
     REQUIRE(cov->kind == FURAX_NOISE_BANDED, "the covariance must be a banded noise handle");
@@ -663,7 +664,8 @@ furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_
     REQUIRE(valid_dtype(dtype), "unknown dtype %d", dtype);
     REQUIRE(maxiter >= 0 && maxiter <= 1000000, "maxiter out of range");
     REQUIRE(tol >= 0.0, "tol must be >= 0");
-    return gapfill(cov, d, valid, n_real, out, dtype, maxiter, tol, iters_out, (cudaStream_t)stream);
+    REQUIRE(valid_dtype(precision), "unknown precision %d", precision);
+    return gapfill(cov, d, valid, n_real, out, dtype, maxiter, tol, precision, iters_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------- templates

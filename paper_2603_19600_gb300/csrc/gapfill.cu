@@ -69,10 +69,24 @@ __global__ void gf_start_kernel(int64_t ndet, GfDet *__restrict__ sc)
     s.rr_new = 0.0;
 }
 
-// q = S q (masked band product of p); pq[det] += p . q.
+// FP32 copy of an FP64 TOD (the operand of the FP32 band product).
+__global__ void __launch_bounds__(FT) gf_to_f32_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                       const double *__restrict__ x, float *__restrict__ x32)
+{
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t i = tod_index(ob, tl, u);
+        x32[i] = (float)x[i];
+    }
+}
+
+// q = S (N p) (the band product nq, FP64 or FP32); pq[det] += p . q.
+template <typename QT>
 __global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                    const uint8_t *__restrict__ valid, const double *__restrict__ p,
-                                                   double *__restrict__ q, GfDet *__restrict__ sc)
+                                                   const QT *__restrict__ nq, double *__restrict__ q,
+                                                   GfDet *__restrict__ sc)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
@@ -80,7 +94,7 @@ __global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tile
     double acc = 0.0;
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
-        const double qv = valid[i] ? q[i] : 0.0;
+        const double qv = valid[i] ? (double)nq[i] : 0.0;
         q[i] = qv;
         acc += p[i] * qv;
     }
@@ -148,23 +162,24 @@ __global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ til
 }
 
 // out = d on observed samples, n + (N y) in the gaps.
-template <typename DT>
+template <typename DT, typename QT>
 __global__ void __launch_bounds__(FT) gf_fill_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                      const DT *__restrict__ d, const DT *__restrict__ nr,
-                                                     const uint8_t *__restrict__ valid, const double *__restrict__ ny,
+                                                     const uint8_t *__restrict__ valid, const QT *__restrict__ ny,
                                                      DT *__restrict__ out)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
-        out[i] = valid[i] ? d[i] : (DT)((double)nr[i] + ny[i]);
+        out[i] = valid[i] ? d[i] : (DT)((double)nr[i] + (double)ny[i]);
     }
 }
 
 furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, const void *nr, void *out, int dtype,
-                     int maxiter, double tol, int32_t *iters_out, cudaStream_t st)
+                     int maxiter, double tol, int precision, int32_t *iters_out, cudaStream_t st)
 {
+    const bool f32 = precision == FURAX_F32;   // band product in FP32, vectors and scalars in FP64
     const int64_t ns = n->nsamp_total, nd = n->ndet_total;
     if (ns == 0 || nd == 0) return FURAX_OK;
     const unsigned g = (unsigned)n->n_tiles;
@@ -180,6 +195,11 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
     alloc((void **)&p, sizeof(double) * ns);
     alloc((void **)&q, sizeof(double) * ns);
     alloc((void **)&sc, sizeof(GfDet) * nd);
+    float *x32 = nullptr, *n32 = nullptr;
+    if (f32) {
+        alloc((void **)&x32, sizeof(float) * ns);
+        alloc((void **)&n32, sizeof(float) * ns);
+    }
     std::vector<GfDet> h(nd);
     bool all_done = false;
     if (!rc) rc = check_cuda(cudaMemsetAsync(sc, 0, sizeof(GfDet) * nd, st), "memset");
@@ -195,8 +215,15 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
         rc = check_launch("gap filling (start)");
     }
     for (int it = 0; !rc && it < maxiter && !all_done; ++it) {
-        if ((rc = launch_ninv(n, p, q, FURAX_F64, st))) break;   // q = N p
-        gf_pq_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, sc);
+        if (f32) {   // N p in FP32
+            gf_to_f32_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, x32);
+            count_launches(1);
+            if ((rc = launch_ninv(n, x32, n32, FURAX_F32, st))) break;
+            gf_pq_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, n32, q, sc);
+        } else {
+            if ((rc = launch_ninv(n, p, q, FURAX_F64, st))) break;
+            gf_pq_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, q, sc);
+        }
         gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
         gf_update_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, q, y, r, sc);
         gf_beta_kernel<<<dg, 128, 0, st>>>(nd, tol * tol, sc);
@@ -211,20 +238,32 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
             for (const GfDet &s : h) all_done = all_done && s.done;
         }
     }
-    if (!rc) rc = launch_ninv(n, y, q, FURAX_F64, st);   // q = N y
+    if (!rc && f32) {   // N y
+        gf_to_f32_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, y, x32);
+        count_launches(1);
+        rc = launch_ninv(n, x32, n32, FURAX_F32, st);
+    } else if (!rc) {
+        rc = launch_ninv(n, y, q, FURAX_F64, st);
+    }
     if (!rc) {
-        if (dtype == FURAX_F64)
-            gf_fill_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const double *)d, (const double *)nr, valid,
-                                                      q, (double *)out);
+        if (dtype == FURAX_F64 && f32)
+            gf_fill_kernel<double, float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const double *)d, (const double *)nr,
+                                                             valid, n32, (double *)out);
+        else if (dtype == FURAX_F64)
+            gf_fill_kernel<double, double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const double *)d, (const double *)nr,
+                                                              valid, q, (double *)out);
+        else if (f32)
+            gf_fill_kernel<float, float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const float *)d, (const float *)nr,
+                                                            valid, n32, (float *)out);
         else
-            gf_fill_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const float *)d, (const float *)nr, valid,
-                                                     q, (float *)out);
+            gf_fill_kernel<float, double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, (const float *)d, (const float *)nr,
+                                                             valid, q, (float *)out);
         count_launches(1);
         rc = check_launch("gap filling (fill)");
     }
     if (!rc) rc = check_cuda(cudaMemcpyAsync(h.data(), sc, sizeof(GfDet) * nd, cudaMemcpyDeviceToHost, st), "read");
     if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "gap filling");
-    cudaFree(y); cudaFree(r); cudaFree(p); cudaFree(q); cudaFree(sc);
+    cudaFree(y); cudaFree(r); cudaFree(p); cudaFree(q); cudaFree(sc); cudaFree(x32); cudaFree(n32);
     if (rc) return rc;
     all_done = true;
     for (int64_t i = 0; i < nd; ++i) {

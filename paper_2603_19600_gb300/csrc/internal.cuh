@@ -309,7 +309,7 @@ furax_status tpl_gram_out(const furax_templates *tp, double *out, cudaStream_t s
 // out = F_T in for a TOD (in != out).
 // Gap filling by constrained realisation (gapfill.cu); n holds the covariance band.
 furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, const void *nr, void *out, int dtype,
-                     int maxiter, double tol, int32_t *iters_out, cudaStream_t st);
+                     int maxiter, double tol, int precision, int32_t *iters_out, cudaStream_t st);
 furax_status deproject_apply(const furax_templates *tp, const void *in, void *out, int dtype, cudaStream_t st);
 
 }  // namespace fx

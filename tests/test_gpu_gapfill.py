@@ -111,3 +111,25 @@ def test_gapfill_full_scale_sampled(fx, dev):
         gap = ~valid[r]
         assert np.array_equal(got[r][valid[r]], d[r][valid[r]])
         assert rel(got[r][gap], ref[0][gap]) < 1e-5
+
+
+@pytest.mark.parametrize("ntaps", [64, 300])
+def test_gapfill_fp32_operator(fx, dev, ntaps):
+    """precision f32: N applied in FP32, CG vectors and scalars in FP64; the filled values follow
+    the oracle to the FP32 band product's accuracy."""
+    obs, cov, d, n, valid = make(ntaps, 100 + ntaps)
+    P = fx.Pointing.from_observations(obs, mode="cache_f32", device=dev)
+    N = fx.Noise.banded(P, np.concatenate(cov))
+    out, iters, ok = fx.gapfill(N, torch.as_tensor(cat(d), device=dev), torch.as_tensor(cat(valid), device=dev),
+                                torch.as_tensor(cat(n), device=dev), maxiter=2000, tol=1e-8, precision="f32")
+    assert ok
+    got = out.cpu().numpy()
+    off = 0
+    for o, c, di, ni, vi in zip(obs, cov, d, n, valid):
+        m = o.ndet * o.nsamp
+        ref, _ = og.gapfill(c, di, vi, ni, tol=1e-13)
+        gi = got[off:off + m].reshape(o.ndet, o.nsamp)
+        assert np.array_equal(gi[vi], di[vi])
+        if (~vi).any():
+            assert rel(gi[~vi], ref[~vi]) < 1e-5, (o.ndet, o.nsamp)
+        off += m
