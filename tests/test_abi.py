@@ -56,6 +56,18 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert lib.furax_pointing_apply(None, None, 0, None, 0, None) == -1
     assert lib.furax_mapmaker_cg(None, None, None, 0, None, None, None, None, None) == -1
     assert lib.furax_noise_inv_apply(None, None, None, 0, None) == -1
+    # template deprojection, overlap-save and gap-filling entry points
+    assert lib.furax_templates_create(None, None, 1, None, ctypes.byref(out)) == -1
+    assert out.value is None
+    assert lib.furax_templates_create(None, None, 1, None, None) == -1
+    assert lib.furax_templates_gram(None, None, None) == -1
+    assert lib.furax_deproject_apply(None, None, None, 0, None) == -1
+    assert b"templates" in lib.furax_last_error()
+    assert lib.furax_ptfp_apply(None, None, None, None, 0, 0, None) == -1
+    assert lib.furax_mapmaker_cg_deproject(None, None, 0, None, None, None, None, None, None) == -1
+    assert lib.furax_gapfill(None, None, None, None, None, 0, 10, ctypes.c_double(1e-8), 1, None, None) == -1
+    assert b"covariance" in lib.furax_last_error()
+    assert lib.furax_templates_destroy(None) == 0
 
 
 def test_python_binding_names_match_c_abi():

@@ -133,3 +133,16 @@ def test_gapfill_fp32_operator(fx, dev, ntaps):
         if (~vi).any():
             assert rel(gi[~vi], ref[~vi]) < 1e-5, (o.ndet, o.nsamp)
         off += m
+
+
+def test_gapfill_rejects_a_white_handle(fx, dev):
+    o = synth.Observation(8, synth.satellite_scan(100), synth.hex_focal_plane(2))
+    P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
+    W = fx.Noise.white(P, np.ones(2))
+    x = torch.zeros(P.nsamp_total, device=dev)
+    with pytest.raises(ValueError):
+        fx.gapfill(W, x, torch.ones_like(x, dtype=torch.uint8), x)
+    out = torch.empty_like(x)
+    with pytest.raises(fx.FuraxError) as e:
+        fx._native.furax_gapfill(W.handle, 2, x, torch.ones_like(x, dtype=torch.uint8), x, out)
+    assert e.value.code == -1
