@@ -44,7 +44,7 @@ struct TmaSmem {
     float s[kRawStages][kRawN];
     float xs[kXsStages][XS];
     alignas(16) float taps[kXsStages][2 * kBandPad];   // band in tap order as (c_|j-63|, c_|j-63|) pairs
-    float4 amp[kRawStages];                            // TPL 2: the tile detector's template amplitudes
+    alignas(16) float4 amp[kRawStages];                // TPL 2: the tile detector's template amplitudes
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
@@ -145,12 +145,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const ObsInfo ob = pv.obs[tl.obs];
             const TileSpan sp = tile_span(tl, ob, halo);
             const uint32_t bytes = (uint32_t)sp.n * 4u;
-            // written before the arrive below, which releases it to the threads waiting on the stage
-            if constexpr (TPL == 2) S.amp[r] = x32[tpl.base + ob.det_off + tl.det];
-            mbar_expect_tx(&S.raw_full[r], 3u * bytes);
+            mbar_expect_tx(&S.raw_full[r], 3u * bytes + (TPL == 2 ? (uint32_t)sizeof(float4) : 0u));
             bulk_g2s(S.pix[r], pv.pix + sp.g0, bytes, &S.raw_full[r]);
             bulk_g2s(S.c[r], pv.c32 + sp.g0, bytes, &S.raw_full[r]);
             bulk_g2s(S.s[r], pv.s32 + sp.g0, bytes, &S.raw_full[r]);
+            // the tile detector's amplitudes ride on the same barrier (16 bytes, 16-byte aligned)
+            if constexpr (TPL == 2)
+                bulk_g2s(&S.amp[r], x32 + tpl.base + ob.det_off + tl.det, (uint32_t)sizeof(float4), &S.raw_full[r]);
         }
         // Copies into a stage complete its current phase; wait for the last one issued into each
         // stage so that no copy is still writing when the CTA exits.
