@@ -217,7 +217,9 @@ __global__ void __launch_bounds__(FT) tpl_project_kernel(const Tile *__restrict_
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = pv.obs[tl.obs];
     const int64_t gdet = ob.det_off + tl.det;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const T h = ob.nsamp > 1 ? T(2) / T(ob.nsamp - 1) : T(0);
+    // interior samples: power sums pw[m] = sum u tau^m, combined with the band's moments at the end
+    T acc[4] = {T(0), T(0), T(0), T(0)}, pw[4] = {T(0), T(0), T(0), T(0)};
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t t = tl.t0 + u;
         T val;
@@ -229,10 +231,27 @@ __global__ void __launch_bounds__(FT) tpl_project_kernel(const Tile *__restrict_
             if (pix < 0) continue;
             val = map_value<T>(x, ob.map_off + pix, c, s);
         }
-        T w[4];
-        wt_eval<T>(nv, tv, gdet, ob.nsamp, t, w);
+        if (t >= tv.halo && t + tv.halo < ob.nsamp) {
+            const T tau = tpl_tau<T>(t, ob.nsamp, h);
+            T v = val;
+            pw[0] += v; v *= tau;
+            pw[1] += v; v *= tau;
+            pw[2] += v; v *= tau;
+            pw[3] += v;
+        } else {
+            T w[4];
+            wt_eval<T>(nv, tv, gdet, ob.nsamp, t, w);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) acc[l] += w[l] * val;
+            for (int l = 0; l < 4; ++l) acc[l] += w[l] * val;
+        }
+    }
+    {   // interior (W P_l)(tau) = mu0 P_l(tau) + (mu2 h^2 / 2) P_l''(tau)
+        const double2 m = tv.mom[gdet];
+        const T mu0 = T(m.x), k2 = T(m.y) * h * h * T(0.5);
+        acc[0] += mu0 * pw[0];
+        acc[1] += mu0 * pw[1];
+        acc[2] += mu0 * (T(1.5) * pw[2] - T(0.5) * pw[0]) + T(3) * k2 * pw[0];
+        acc[3] += mu0 * (T(2.5) * pw[3] - T(1.5) * pw[1]) + T(15) * k2 * pw[1];
     }
     cta_sum<4, T>(acc);
     if (threadIdx.x == 0)
@@ -257,10 +276,31 @@ __global__ void tpl_solve_kernel(int64_t ndet, const double *__restrict__ ginv, 
     }
 }
 
+// sum_l b_l (W P_l)(t) for one detector stream: in the interior the cubic c0 + c1 tau + c2 tau^2 + c3 tau^3,
+// whose coefficients are fixed per detector; term by term within a half-band of either end.
+template <typename T>
+struct TplPoly {
+    T h, c[4];
+    __device__ __forceinline__ TplPoly(const TplView &tv, int64_t gdet, int64_t ns, const T (&bv)[4])
+    {
+        h = ns > 1 ? T(2) / T(ns - 1) : T(0);
+        const double2 m = tv.mom[gdet];
+        const T mu0 = T(m.x), k2 = T(m.y) * h * h * T(0.5);
+        c[0] = mu0 * (bv[0] - T(0.5) * bv[2]) + T(3) * k2 * bv[2];
+        c[1] = mu0 * (bv[1] - T(1.5) * bv[3]) + T(15) * k2 * bv[3];
+        c[2] = T(1.5) * mu0 * bv[2];
+        c[3] = T(2.5) * mu0 * bv[3];
+    }
+};
+
 template <typename T>
 __device__ __forceinline__ T tpl_value(const NoiseView &nv, const TplView &tv, int64_t gdet, int64_t ns, int64_t t,
-                                       const T (&bv)[4])
+                                       const T (&bv)[4], const TplPoly<T> &pl)
 {
+    if (t >= tv.halo && t + tv.halo < ns) {
+        const T tau = tpl_tau<T>(t, ns, pl.h);
+        return ((pl.c[3] * tau + pl.c[2]) * tau + pl.c[1]) * tau + pl.c[0];
+    }
     T w[4];
     wt_eval<T>(nv, tv, gdet, ns, t, w);
     return bv[0] * w[0] + bv[1] * w[1] + bv[2] * w[2] + bv[3] * w[3];
@@ -278,12 +318,13 @@ __global__ void __launch_bounds__(FT) tpl_scatter_kernel(const Tile *__restrict_
     T bv[4];
 #pragma unroll
     for (int l = 0; l < 4; ++l) bv[l] = T(tv.b[4 * gdet + l]);
+    const TplPoly<T> pl(tv, gdet, ob.nsamp, bv);
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t t = tl.t0 + u;
         T c, s;
         const int32_t pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
         if (pix < 0) continue;
-        const T v = -tpl_value<T>(nv, tv, gdet, ob.nsamp, t, bv);
+        const T v = -tpl_value<T>(nv, tv, gdet, ob.nsamp, t, bv, pl);
         const int64_t gp = ob.map_off + pix;
         if constexpr (ACC == FURAX_ACC_F32) {
             red_add_v4(hi + gp, make_float4(float(v), float(v * c), float(v * s), 0.f));
@@ -308,10 +349,11 @@ __global__ void __launch_bounds__(FT) tpl_tod_kernel(const Tile *__restrict__ ti
     T bv[4];
 #pragma unroll
     for (int l = 0; l < 4; ++l) bv[l] = T(tv.b[4 * gdet + l]);
+    const TplPoly<T> pl(tv, gdet, ob.nsamp, bv);
     T *row = y + ob.tod_off + (int64_t)tl.det * ob.nsamp;
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t t = tl.t0 + u;
-        row[t] -= tpl_value<T>(nv, tv, gdet, ob.nsamp, t, bv);
+        row[t] -= tpl_value<T>(nv, tv, gdet, ob.nsamp, t, bv, pl);
     }
 }
 
