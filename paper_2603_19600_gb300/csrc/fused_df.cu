@@ -10,6 +10,8 @@
 // an evaluation in twice the FP32 precision (~2^-48) followed by rounding. The projection and
 // the per-pixel sums stay in FP64 (a few FP64 operations per sample).
 #include "tile.cuh"
+#include "dfloat.cuh"
+#include "tpl_eval.cuh"
 
 namespace fx {
 
@@ -55,12 +57,6 @@ __device__ __forceinline__ void band_product_df(const float *__restrict__ xh, co
             }
         }
     }
-}
-
-__device__ __forceinline__ void split_df(double v, float &hi, float &lo)
-{
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
 }
 
 constexpr size_t kDfSmem = sizeof(float) * (2 * XS + 2 * MAXTAPS) + sizeof(float2) * 2 * CS + sizeof(int32_t) * CS;
@@ -154,18 +150,6 @@ __global__ void __launch_bounds__(FT, 2) fused_df_kernel(const Tile *__restrict_
 // binary64 value is built from the binary32 encoding, so no FP64 arithmetic is issued); tails,
 // which are ~2^-24 of the heads, are accumulated in FP32 and folded in afterwards.
 // ------------------------------------------------------------------------------------
-
-// Compensated step with an exact FP32 input (no input low word).
-__device__ __forceinline__ void dot2_step_x(float ch, float cl, float x, float &S, float &E)
-{
-    const float p = __fmul_rn(ch, x);
-    const float e = __fmaf_rn(ch, x, -p);
-    const float s = __fadd_rn(S, p);
-    const float bv = __fsub_rn(s, S);
-    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bv)), __fsub_rn(p, bv));
-    S = s;
-    E = __fmaf_rn(cl, x, __fadd_rn(E, __fadd_rn(err, e)));
-}
 
 // The taps are walked in blocks of JB (a rolled loop), each block unrolled over JB taps x R
 // outputs from a register window of R + JB - 1 inputs: a fully unrolled 127 x R body does not fit
@@ -322,10 +306,15 @@ __device__ __forceinline__ int32_t sample_df(const PointingView &pv, const ObsIn
 constexpr size_t kDfRhsSmem = sizeof(float4) * kBandPad + sizeof(float2) * kBandPad + sizeof(float) * (XS + CS + 2 * MAXTAPS);
 static_assert(sizeof(float4) * kBandPad % 16 == 0 && sizeof(float2) * kBandPad % 16 == 0, "coefficient arrays stay 16-byte aligned");
 
-template <int MODE, bool BANDED>
+// TPL: the template correction of the deprojected right-hand side is folded in, y -= (W T) b for
+// amplitudes b already solved from d: in the interior of a stream (W T b)(t) is a cubic in the
+// offset j of t from the middle sample of the tile's own samples (no extrapolation in tau), evaluated by Horner's rule in double-FP32 from
+// coefficients the CTA forms once in FP64; near the ends of the stream it is summed term by term
+// in FP64.
+template <int MODE, bool BANDED, bool TPL>
 __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
                                                        const float *__restrict__ d, double *__restrict__ acc64,
-                                                       float4 *__restrict__ acc_lo)
+                                                       float4 *__restrict__ acc_lo, TplView tv)
 {
     extern __shared__ __align__(16) float rsm[];
     float4 *C4 = reinterpret_cast<float4 *>(rsm);            // [kBandPad] (c_hi, c_hi, -c_hi, -c_hi), tap order
@@ -351,6 +340,19 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
         if (j < kBand && k < nv.ntaps) split_df(nv.p64[gdet * nv.ntaps + k], h, l);
         C4[j] = make_float4(h, h, -h, -h);
         CL2[j] = make_float2(l, l);
+    }
+    __shared__ float2 ecoef[4];   // TPL: coefficients of the tile's cubic in j, double-FP32
+    if constexpr (TPL) {
+        if (threadIdx.x == 0) {
+            const double h = ob.nsamp > 1 ? 2.0 / (double)(ob.nsamp - 1) : 0.0;
+            const double2 m = tv.mom[gdet];
+            const double bv[4] = {tv.b[4 * gdet], tv.b[4 * gdet + 1], tv.b[4 * gdet + 2], tv.b[4 * gdet + 3]};
+            double c[4], e[4];
+            tpl_cubic(m.x, m.y * h * h * 0.5, bv, c);
+            cubic_shift(c, tpl_tau_ref(tile.t0 + (tile.len >> 1), ob.nsamp), h, e);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) split_df(e[i], ecoef[i].x, ecoef[i].y);
+        }
     }
     const int nload = tile.len + 2 * halo;
     const int64_t row = ob.tod_off + tile.det * ob.nsamp;
@@ -391,7 +393,25 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
         float ch, cl, sh, sl;
         const int32_t pix = sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl);
         if (pix < 0) continue;
-        const float yh = xs[spos(k)], ylo = yl[spos(k)];
+        float yh = xs[spos(k)], ylo = yl[spos(k)];
+        if constexpr (TPL) {
+            const int64_t t = tile.t0 + k;
+            if (tpl_interior(tv, t, ob.nsamp)) {
+                const float j = (float)(k - (tile.len >> 1));
+                float vh = ecoef[3].x, vl = ecoef[3].y;
+                df_horner(vh, vl, j, ecoef[2].x, ecoef[2].y);
+                df_horner(vh, vl, j, ecoef[1].x, ecoef[1].y);
+                df_horner(vh, vl, j, ecoef[0].x, ecoef[0].y);
+                df_add(yh, ylo, -vh, -vl);
+            } else {
+                double w[4];
+                wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
+                double v = (double)yh + (double)ylo;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) v -= tv.b[4 * gdet + l] * w[l];
+                split_df(v, yh, ylo);
+            }
+        }
         const float qc = __fmul_rn(yh, ch), qs = __fmul_rn(yh, sh);
         const float ec = __fmaf_rn(yh, ch, -qc), es = __fmaf_rn(yh, sh, -qs);
         const float lc = __fadd_rn(ec, __fmaf_rn(ylo, ch, __fmul_rn(yh, cl)));
@@ -417,14 +437,17 @@ __global__ void fold_lo_kernel(const float4 *__restrict__ lo, double *__restrict
 
 template <int MODE, bool B>
 static furax_status run_df_rhs(const furax_pointing *p, const furax_noise *n, const float *d, double *a64, float4 *lo,
-                               cudaStream_t st)
+                               cudaStream_t st, const TplView *tv)
 {
-    return launch_dyn(df_rhs_kernel<MODE, B>, (unsigned)p->n_tiles, FT, kDfRhsSmem, st, p->d_tiles, p->view(), n->view(),
-                      d, a64, lo);
+    if (tv)
+        return launch_dyn(df_rhs_kernel<MODE, B, true>, (unsigned)p->n_tiles, FT, kDfRhsSmem, st, p->d_tiles, p->view(),
+                          n->view(), d, a64, lo, *tv);
+    return launch_dyn(df_rhs_kernel<MODE, B, false>, (unsigned)p->n_tiles, FT, kDfRhsSmem, st, p->d_tiles, p->view(),
+                      n->view(), d, a64, lo, TplView{});
 }
 
 static furax_status launch_df_rhs_f32(const furax_pointing *p, const furax_noise *n, const float *d, double *a64,
-                                      cudaStream_t st)
+                                      cudaStream_t st, const TplView *tv)
 {
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     furax_status rc;
@@ -434,16 +457,16 @@ static furax_status launch_df_rhs_f32(const furax_pointing *p, const furax_noise
     const bool b = n->kind == FURAX_NOISE_BANDED;
     switch (p->mode) {
     case FURAX_POINTING_ON_THE_FLY:
-        rc = b ? run_df_rhs<0, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<0, false>(p, n, d, a64, pm->ws_df_lo, st);
+        rc = b ? run_df_rhs<0, true>(p, n, d, a64, pm->ws_df_lo, st, tv) : run_df_rhs<0, false>(p, n, d, a64, pm->ws_df_lo, st, tv);
         break;
     case FURAX_POINTING_CACHE_F32:
-        rc = b ? run_df_rhs<1, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<1, false>(p, n, d, a64, pm->ws_df_lo, st);
+        rc = b ? run_df_rhs<1, true>(p, n, d, a64, pm->ws_df_lo, st, tv) : run_df_rhs<1, false>(p, n, d, a64, pm->ws_df_lo, st, tv);
         break;
     case FURAX_POINTING_CACHE_MIXED:
-        rc = b ? run_df_rhs<3, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<3, false>(p, n, d, a64, pm->ws_df_lo, st);
+        rc = b ? run_df_rhs<3, true>(p, n, d, a64, pm->ws_df_lo, st, tv) : run_df_rhs<3, false>(p, n, d, a64, pm->ws_df_lo, st, tv);
         break;
     default:
-        rc = b ? run_df_rhs<2, true>(p, n, d, a64, pm->ws_df_lo, st) : run_df_rhs<2, false>(p, n, d, a64, pm->ws_df_lo, st);
+        rc = b ? run_df_rhs<2, true>(p, n, d, a64, pm->ws_df_lo, st, tv) : run_df_rhs<2, false>(p, n, d, a64, pm->ws_df_lo, st, tv);
     }
     if (rc) return rc;
     if ((rc = check_launch("double-FP32 P^T N^-1 d"))) return rc;
@@ -479,11 +502,16 @@ static furax_status dispatch_df(const furax_pointing *p, const furax_noise *n, c
 }
 
 furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, const double *x, const void *d, int d_t,
-                             double *acc64, cudaStream_t st)
+                             double *acc64, cudaStream_t st, const furax_templates *tp)
 {
     if (p->n_tiles == 0) return FURAX_OK;
     furax_status rc;
-    if (d && d_t == FURAX_F32) return launch_df_rhs_f32(p, n, (const float *)d, acc64, st);
+    if (tp && !(d && d_t == FURAX_F32))
+        return set_error(FURAX_EINVAL, "internal: the template correction is folded only into the FP32-data right-hand side");
+    if (d && d_t == FURAX_F32) {
+        const TplView tv = tp ? tp->view() : TplView{};
+        return launch_df_rhs_f32(p, n, (const float *)d, acc64, st, tp ? &tv : nullptr);
+    }
     if (!d) rc = dispatch_df<false, double>(p, n, x, (const double *)nullptr, acc64, st);
     else if (d_t == FURAX_F64) rc = dispatch_df<true, double>(p, n, nullptr, (const double *)d, acc64, st);
     else rc = dispatch_df<true, float>(p, n, nullptr, (const float *)d, acc64, st);
@@ -499,7 +527,8 @@ static furax_status prep_df_mode_band()
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, false, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, float>, kDfSmem);
-    if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B>, kDfRhsSmem);
+    if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, false>, kDfRhsSmem);
+    if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, true>, kDfRhsSmem);
     return rc;
 }
 

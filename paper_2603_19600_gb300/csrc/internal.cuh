@@ -264,8 +264,10 @@ furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, con
                               cudaStream_t st);
 // FP64-accurate operator on FP32 units (double-FP32 band product): acc64 += P^T N^-1 P x, or
 // acc64 += P^T N^-1 d when d != nullptr.
+// tp (FP32 d only): fold the template correction -P^T (W T) b of the deprojected right-hand side into
+// the same pass, with b already solved by launch_tpl_rhs_amplitudes.
 furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, const double *x, const void *d, int d_t,
-                             double *acc64, cudaStream_t st);
+                             double *acc64, cudaStream_t st, const furax_templates *tp = nullptr);
 // b = P^T N^-1 d accumulated into acc64 (FP64 stencil)
 furax_status launch_rhs_f64(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, double *acc64,
                             cudaStream_t st);
@@ -297,6 +299,9 @@ furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, c
 double *tpl_fused_target(const furax_templates *tp, const furax_pointing *p);
 // acc64 -= P^T (W T) G^-1 (W T)^T d (FP64 arithmetic).
 furax_status launch_tpl_rhs(const furax_templates *tp, const void *d, int d_t, double *acc64, cudaStream_t st);
+// b = G^-1 (W T)^T d only (the first half of launch_tpl_rhs), for a right-hand side that folds the
+// correction into its own pass.
+furax_status launch_tpl_rhs_amplitudes(const furax_templates *tp, const void *d, int d_t, cudaStream_t st);
 // The inner FP32 solve runs on the augmented system [m; amplitudes] (one fused pass per iteration).
 bool tpl_augmented(const furax_templates *tp, int precision);
 // minv and valid of the amplitude pseudo-pixels: the 3x3 leading block of G^-1.

@@ -772,6 +772,10 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     if (o->d_ready && (rc = check_cuda(cudaStreamWaitEvent(st, (cudaEvent_t)o->d_ready, 0), "wait for d")))
         return rc;
     if ((rc = check_cuda(cudaMemsetAsync(w->acc64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
+    // the double-FP32 pass from FP32 data subtracts the template correction itself, with the
+    // amplitudes solved beforehand
+    const bool tpl_folded = tp && !long_band(n) && o->precision != FURAX_F64 && d_t == FURAX_F32;
+    if (tpl_folded && (rc = launch_tpl_rhs_amplitudes(tp, d, d_t, st))) return rc;
     if (long_band(n)) {
         // TOD workspaces exist before any stream capture of the iteration
         if ((rc = tod_ws(p))) return rc;
@@ -779,9 +783,10 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     } else if (o->precision == FURAX_F64) {
         if ((rc = timed(1, st, [&] { return launch_rhs_f64(p, n, d, d_t, w->acc64, st); }))) return rc;
     } else {
-        if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, nullptr, d, d_t, w->acc64, st); }))) return rc;
+        if ((rc = timed(2, st, [&] { return launch_fused_df(p, n, nullptr, d, d_t, w->acc64, st, tpl_folded ? tp : nullptr); })))
+            return rc;
     }
-    if (tp && (rc = launch_tpl_rhs(tp, d, d_t, w->acc64, st))) return rc;
+    if (tp && !tpl_folded && (rc = launch_tpl_rhs(tp, d, d_t, w->acc64, st))) return rc;
     if ((rc = launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, w->acc64, w->valid, w->bfull, st))) return rc;
     if (valid_out && (rc = check_cuda(cudaMemcpyAsync(valid_out, w->valid, np, cudaMemcpyDeviceToDevice, st), "copy mask")))
         return rc;

@@ -11,6 +11,8 @@
 //   project  a_det = (W T)^T u over the detector's stream (u = P x, or a TOD),
 //   solve    b_det = G_det^-1 a_det,
 //   scatter  acc -= P^T (W T) b   (or, for a TOD, y -= (W T) b).
+// For the right-hand side of FP32 data in the mixed-precision solver the scatter is not a pass of
+// its own: the double-FP32 pass that forms P^T W d subtracts (W T) b from W d per sample.
 //
 // (W T)(t) needs no band product. For a polynomial p of degree <= 3 and a symmetric band whose
 // full width fits around t,
@@ -19,68 +21,10 @@
 // moments of a symmetric band vanish and the fourth derivative of p is zero. Within a half-width
 // of either end of the stream the truncated sum is taken term by term.
 #include "tile.cuh"
+#include "tpl_eval.cuh"
+#include "dfloat.cuh"
 
 namespace fx {
-
-// P_0..P_3 at tau (closed forms).
-template <typename T>
-__device__ __forceinline__ void legendre4(T tau, T (&L)[4])
-{
-    L[0] = T(1);
-    L[1] = tau;
-    L[2] = T(1.5) * tau * tau - T(0.5);
-    L[3] = tau * (T(2.5) * tau * tau - T(1.5));
-}
-
-template <typename T>
-__device__ __forceinline__ T tpl_tap(const NoiseView &nv, int64_t gdet, int k)
-{
-    if (nv.kind == FURAX_NOISE_WHITE) {
-        if (k != 0) return T(0);
-        if constexpr (sizeof(T) == 4) return nv.p32[gdet];
-        else return nv.p64[gdet];
-    }
-    if constexpr (sizeof(T) == 4) return nv.p32[gdet * nv.ntaps + k];
-    else return nv.p64[gdet * nv.ntaps + k];
-}
-
-template <typename T>
-__device__ __forceinline__ T tpl_tau(int64_t t, int64_t ns, T h)
-{
-    return ns > 1 ? T(t) * h - T(1) : T(0);
-}
-
-// w[l] = (W P_l)(t) for one detector stream of ns samples.
-template <typename T>
-__device__ __forceinline__ void wt_eval(const NoiseView &nv, const TplView &tv, int64_t gdet, int64_t ns, int64_t t,
-                                        T (&w)[4])
-{
-    const T h = ns > 1 ? T(2) / T(ns - 1) : T(0);
-    if (t >= tv.halo && t + tv.halo < ns) {
-        const double2 m = tv.mom[gdet];
-        const T mu0 = T(m.x);
-        const T k2 = T(m.y) * h * h * T(0.5);
-        const T tau = tpl_tau<T>(t, ns, h);
-        T L[4];
-        legendre4(tau, L);
-        w[0] = mu0;
-        w[1] = mu0 * tau;
-        w[2] = mu0 * L[2] + T(3) * k2;
-        w[3] = mu0 * L[3] + T(15) * k2 * tau;
-        return;
-    }
-#pragma unroll
-    for (int l = 0; l < 4; ++l) w[l] = T(0);
-    for (int k = -tv.halo; k <= tv.halo; ++k) {
-        const int64_t s = t + k;
-        if (s < 0 || s >= ns) continue;
-        const T c = tpl_tap<T>(nv, gdet, k < 0 ? -k : k);
-        T L[4];
-        legendre4(tpl_tau<T>(s, ns, h), L);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) w[l] += c * L[l];
-    }
-}
 
 // Sum of v[0..N) over the CTA (FT threads); the result is valid in thread 0.
 template <int N, typename T>
@@ -258,6 +202,88 @@ __global__ void __launch_bounds__(FT) tpl_project_kernel(const Tile *__restrict_
         for (int l = 0; l <= tv.order; ++l) red_add_f64(a + 4 * gdet + l, scale * (double)acc[l]);
 }
 
+// a[det] += scale sum_t (W T)(t) d_t for FP32 data d, FP64-accurate on FP32 units. Interior samples
+// (band fully inside the stream) contribute through the power sums Q_i = sum d_t j^i (i <= 3) of
+// the offset j = t - t_c from the middle sample t_c of the tile (so that |tau_c| <= 1 and the
+// re-expansion does not extrapolate), accumulated as double-FP32 compensated
+// dot products with exact multipliers (j and j^2 are exact in binary32 for |j| <= 2048; j^3 is
+// split exactly into two words); the CTA combines them in FP64 with tau = tau_c + h j and the
+// band's moments. Samples near the ends of the stream take the FP64 term-by-term sum.
+__global__ void __launch_bounds__(FT) tpl_project_tod_df_kernel(const Tile *__restrict__ tiles,
+                                                                const ObsInfo *__restrict__ obs, NoiseView nv,
+                                                                TplView tv, const float *__restrict__ d, double scale,
+                                                                double *__restrict__ a)
+{
+    static_assert(TILE / 2 <= 2048, "offsets and their squares must be exact in binary32");
+    const Tile tl = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tl.obs];
+    const int64_t gdet = ob.det_off + tl.det;
+    const float *row = d + ob.tod_off + (int64_t)tl.det * ob.nsamp;
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+    double edge[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int u = threadIdx.x; u < tl.len; u += FT) {
+        const int64_t t = tl.t0 + u;
+        const float x = row[t];
+        if (tpl_interior(tv, t, ob.nsamp)) {
+            const float j = (float)(u - (tl.len >> 1));
+            const float j2 = __fmul_rn(j, j);
+            const float j3 = __fmul_rn(j2, j), j3l = __fmaf_rn(j2, j, -j3);
+            dot2_step_x(1.f, 0.f, x, S[0], E[0]);
+            dot2_step_x(j, 0.f, x, S[1], E[1]);
+            dot2_step_x(j2, 0.f, x, S[2], E[2]);
+            dot2_step_x(j3, j3l, x, S[3], E[3]);
+        } else {
+            double w[4];
+            wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) edge[l] += w[l] * (double)x;
+        }
+    }
+    // warp sums in double-FP32, then FP64 across the warps
+    __shared__ double red[FT / 32][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float h, l;
+        df_renorm(S[i], E[i], h, l);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, l, o);
+            df_add(h, l, oh, ol);
+        }
+        S[i] = h;
+        E[i] = l;
+    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[threadIdx.x >> 5][i] = (double)S[i] + (double)E[i];
+    // edge samples only occur in a stream's first and last tiles
+    const bool has_edge = tl.t0 < tv.halo || tl.t0 + tl.len + tv.halo > ob.nsamp;
+    if (has_edge) cta_sum<4, double>(edge);
+    else __syncthreads();
+    if (threadIdx.x != 0) return;
+    double Q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Q[i] = 0.0;
+        for (int w = 0; w < FT / 32; ++w) Q[i] += red[w][i];
+    }
+    const double h = ob.nsamp > 1 ? 2.0 / (double)(ob.nsamp - 1) : 0.0;
+    const double tc = tpl_tau_ref(tl.t0 + (tl.len >> 1), ob.nsamp);
+    const double hq1 = h * Q[1], h2q2 = h * h * Q[2], h3q3 = h * h * h * Q[3];
+    // pw[m] = sum d tau^m over the interior samples, tau = tc + h j
+    const double pw0 = Q[0];
+    const double pw1 = tc * Q[0] + hq1;
+    const double pw2 = tc * (tc * Q[0] + 2.0 * hq1) + h2q2;
+    const double pw3 = tc * (tc * (tc * Q[0] + 3.0 * hq1) + 3.0 * h2q2) + h3q3;
+    const double2 m = tv.mom[gdet];
+    const double mu0 = m.x, k2 = m.y * h * h * 0.5;
+    const double v[4] = {mu0 * pw0, mu0 * pw1, mu0 * (1.5 * pw2 - 0.5 * pw0) + 3.0 * k2 * pw0,
+                         mu0 * (2.5 * pw3 - 1.5 * pw1) + 15.0 * k2 * pw1};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        if (l <= tv.order) red_add_f64(a + 4 * gdet + l, scale * (v[l] + (has_edge ? edge[l] : 0.0)));
+}
+
 // b[det] = G^-1 a[det]; a[det] = 0 for the next projection.
 __global__ void tpl_solve_kernel(int64_t ndet, const double *__restrict__ ginv, double *__restrict__ a,
                                  double *__restrict__ b)
@@ -365,14 +391,18 @@ static void project_mode(const furax_templates *tp, const XT *x, const DT *d, cu
 {
     const furax_pointing *p = tp->p;
     const unsigned g = (unsigned)p->n_tiles;
-    const PointingView pv = p->view();
-    const NoiseView nv = tp->n->view();
-    const TplView tv = tp->view();
-    switch (FROM_TOD ? 2 : p->mode) {
-    case FURAX_POINTING_ON_THE_FLY: tpl_project_kernel<0, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
-    case FURAX_POINTING_CACHE_F32: tpl_project_kernel<1, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
-    case FURAX_POINTING_CACHE_MIXED: tpl_project_kernel<3, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
-    default: tpl_project_kernel<2, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
+    if constexpr (FROM_TOD && sizeof(T) == 8 && sizeof(DT) == 4) {   // FP64-accurate from FP32 data
+        tpl_project_tod_df_kernel<<<g, FT, 0, st>>>(p->d_tiles, p->d_obs, tp->n->view(), tp->view(), d, scale, tp->a);
+    } else {
+        const PointingView pv = p->view();
+        const NoiseView nv = tp->n->view();
+        const TplView tv = tp->view();
+        switch (FROM_TOD ? 2 : p->mode) {
+        case FURAX_POINTING_ON_THE_FLY: tpl_project_kernel<0, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
+        case FURAX_POINTING_CACHE_F32: tpl_project_kernel<1, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
+        case FURAX_POINTING_CACHE_MIXED: tpl_project_kernel<3, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
+        default: tpl_project_kernel<2, T, XT, FROM_TOD, DT><<<g, FT, 0, st>>>(p->d_tiles, pv, nv, tv, x, d, scale, tp->a); break;
+        }
     }
 }
 
@@ -419,6 +449,17 @@ furax_status launch_tpl_map(const furax_templates *tp, int precision, int acc, c
     }
     count_launches(projected && precision == FURAX_F32 ? 2 : 3);
     return check_launch("template deprojection (map)");
+}
+
+furax_status launch_tpl_rhs_amplitudes(const furax_templates *tp, const void *d, int d_t, cudaStream_t st)
+{
+    if (tp->p->n_tiles > 0) {
+        if (d_t == FURAX_F64) project_mode<double, double, true, double>(tp, nullptr, (const double *)d, st);
+        else project_mode<double, double, true, float>(tp, nullptr, (const float *)d, st);
+    }
+    solve(tp, st);
+    count_launches(2);
+    return check_launch("template amplitudes of the right-hand side");
 }
 
 furax_status launch_tpl_rhs(const furax_templates *tp, const void *d, int d_t, double *acc64, cudaStream_t st)
