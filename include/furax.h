@@ -335,9 +335,10 @@ furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void 
  * is the unconstrained realisation (the caller's random draws). Per detector, CG from 0 until
  * ||r|| <= tol ||r_0|| or maxiter iterations; precision FURAX_F64 applies N in FP64, FURAX_F32 in
  * FP32 (vectors and scalars stay FP64; the filled values are then good to ~1e-7 relative);
- * iters_out: host int32 [sum ndet] or NULL. Allocates 4 FP64 TOD workspaces (+ 2 FP32) for the
- * call and synchronises stream. FURAX_ENOTCONVERGED when a detector stopped at maxiter (out is
- * still written). */
+ * iters_out: host int32 [sum ndet] or NULL. The first call allocates TOD-sized workspaces in the
+ * handle (3 FP64, plus 1 FP64 for FURAX_F64 or 2 FP32 for FURAX_F32) that later calls reuse and
+ * furax_noise_destroy frees, so calls on one handle must not run concurrently; synchronises
+ * stream. FURAX_ENOTCONVERGED when a detector stopped at maxiter (out is still written). */
 furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,
                            void *out, int32_t dtype, int32_t maxiter, double tol, int32_t precision,
                            int32_t *iters_out, void *stream);

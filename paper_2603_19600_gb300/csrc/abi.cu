@@ -547,6 +547,8 @@ furax_status furax_noise_destroy(furax_noise_t *n)
     cudaDeviceSynchronize();
     cudaFree(n->p64); cudaFree(n->p32); cudaFree(n->diag); cudaFree(n->d_obs); cudaFree(n->d_tiles);
     cudaFree(n->fft_items); cudaFree(n->tw64); cudaFree(n->tw32); cudaFree(n->spec64); cudaFree(n->spec32);
+    cudaFree(n->gf_y); cudaFree(n->gf_r); cudaFree(n->gf_p); cudaFree(n->gf_q); cudaFree(n->gf_x32); cudaFree(n->gf_n32);
+    cudaFree(n->gf_sc);
     delete n;
     return check_launch("noise destroy");
 }

@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(FT) gf_to_f32_kernel(const Tile *__restrict__ 
     }
 }
 
-// q = S (N p) (the band product nq, FP64 or FP32); pq[det] += p . q.
+// q = S (N p) (the band product nq, FP64 or FP32); pq[det] += p . q. The FP64 q is stored (in
+// place over nq); the FP32 one is recomputed from nq by the update, which saves a stored vector.
 template <typename QT>
 __global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                    const uint8_t *__restrict__ valid, const double *__restrict__ p,
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tile
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
         const double qv = valid[i] ? (double)nq[i] : 0.0;
-        q[i] = qv;
+        if constexpr (sizeof(QT) == 8) q[i] = qv;
         acc += p[i] * qv;
     }
     acc = cta_sum_d(acc);
@@ -111,11 +112,13 @@ __global__ void gf_alpha_kernel(int64_t ndet, GfDet *__restrict__ sc)
     s.rr_new = 0.0;
 }
 
-// y += alpha p; r -= alpha q; rr_new[det] += |r|^2.
+// y += alpha p; r -= alpha q; rr_new[det] += |r|^2. q is the stored FP64 S N p, or S applied to the
+// FP32 band product.
+template <typename QT>
 __global__ void __launch_bounds__(FT) gf_update_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
-                                                       const double *__restrict__ p, const double *__restrict__ q,
-                                                       double *__restrict__ y, double *__restrict__ r,
-                                                       GfDet *__restrict__ sc)
+                                                       const uint8_t *__restrict__ valid, const double *__restrict__ p,
+                                                       const QT *__restrict__ q, double *__restrict__ y,
+                                                       double *__restrict__ r, GfDet *__restrict__ sc)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
@@ -125,7 +128,10 @@ __global__ void __launch_bounds__(FT) gf_update_kernel(const Tile *__restrict__ 
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
         y[i] += s.alpha * p[i];
-        const double rv = r[i] - s.alpha * q[i];
+        double qv;
+        if constexpr (sizeof(QT) == 8) qv = q[i];
+        else qv = valid[i] ? (double)q[i] : 0.0;
+        const double rv = r[i] - s.alpha * qv;
         r[i] = rv;
         acc += rv * rv;
     }
@@ -146,10 +152,10 @@ __global__ void gf_beta_kernel(int64_t ndet, double tol2, GfDet *__restrict__ sc
     if (s.rr <= tol2 * s.rr0) s.done = 1;
 }
 
-// p = r + beta p (detectors still iterating).
+// p = r + beta p (detectors still iterating), and its FP32 copy for the next FP32 band product.
 __global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                     const double *__restrict__ r, double *__restrict__ p,
-                                                    const GfDet *__restrict__ sc)
+                                                    float *__restrict__ x32, const GfDet *__restrict__ sc)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
@@ -157,7 +163,9 @@ __global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ til
     if (s.done) return;
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
-        p[i] = r[i] + s.beta * p[i];
+        const double pv = r[i] + s.beta * p[i];
+        p[i] = pv;
+        if (x32) x32[i] = (float)pv;
     }
 }
 
@@ -184,22 +192,23 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
     if (ns == 0 || nd == 0) return FURAX_OK;
     const unsigned g = (unsigned)n->n_tiles;
     const unsigned dg = (unsigned)((nd + 127) / 128);
-    double *y = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
-    GfDet *sc = nullptr;
+    furax_noise *nm = const_cast<furax_noise *>(n);   // workspaces live in the handle
     furax_status rc = FURAX_OK;
-    auto alloc = [&](void **ptr, size_t bytes) {
-        if (!rc) rc = check_cuda(cudaMalloc(ptr, bytes), "gap-filling workspace");
+    auto ensure = [&](void **ptr, size_t bytes) {
+        if (!rc && !*ptr && (rc = check_cuda(cudaMalloc(ptr, bytes), "gap-filling workspace"))) *ptr = nullptr;
     };
-    alloc((void **)&y, sizeof(double) * ns);
-    alloc((void **)&r, sizeof(double) * ns);
-    alloc((void **)&p, sizeof(double) * ns);
-    alloc((void **)&q, sizeof(double) * ns);
-    alloc((void **)&sc, sizeof(GfDet) * nd);
-    float *x32 = nullptr, *n32 = nullptr;
+    ensure((void **)&nm->gf_y, sizeof(double) * ns);
+    ensure((void **)&nm->gf_r, sizeof(double) * ns);
+    ensure((void **)&nm->gf_p, sizeof(double) * ns);
+    if (!f32) ensure((void **)&nm->gf_q, sizeof(double) * ns);   // FP32 band product: q is not stored
+    ensure(&nm->gf_sc, sizeof(GfDet) * nd);
     if (f32) {
-        alloc((void **)&x32, sizeof(float) * ns);
-        alloc((void **)&n32, sizeof(float) * ns);
+        ensure((void **)&nm->gf_x32, sizeof(float) * ns);
+        ensure((void **)&nm->gf_n32, sizeof(float) * ns);
     }
+    double *y = nm->gf_y, *r = nm->gf_r, *p = nm->gf_p, *q = nm->gf_q;
+    GfDet *sc = (GfDet *)nm->gf_sc;
+    float *x32 = nm->gf_x32, *n32 = nm->gf_n32;
     std::vector<GfDet> h(nd);
     bool all_done = false;
     if (!rc) rc = check_cuda(cudaMemsetAsync(sc, 0, sizeof(GfDet) * nd, st), "memset");
@@ -212,22 +221,26 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
                                                      y, r, p, sc);
         gf_start_kernel<<<dg, 128, 0, st>>>(nd, sc);
         count_launches(2);
+        if (f32) {   // the first direction's FP32 copy; later ones come from gf_dir
+            gf_to_f32_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, x32);
+            count_launches(1);
+        }
         rc = check_launch("gap filling (start)");
     }
     for (int it = 0; !rc && it < maxiter && !all_done; ++it) {
         if (f32) {   // N p in FP32
-            gf_to_f32_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, x32);
-            count_launches(1);
             if ((rc = launch_ninv(n, x32, n32, FURAX_F32, st))) break;
-            gf_pq_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, n32, q, sc);
+            gf_pq_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, n32, nullptr, sc);
+            gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
+            gf_update_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, n32, y, r, sc);
         } else {
             if ((rc = launch_ninv(n, p, q, FURAX_F64, st))) break;
             gf_pq_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, q, sc);
+            gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
+            gf_update_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, y, r, sc);
         }
-        gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
-        gf_update_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, p, q, y, r, sc);
         gf_beta_kernel<<<dg, 128, 0, st>>>(nd, tol * tol, sc);
-        gf_dir_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, r, p, sc);
+        gf_dir_kernel<<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, r, p, f32 ? x32 : nullptr, sc);
         count_launches(5);
         if ((rc = check_launch("gap filling (iteration)"))) break;
         if ((it + 1) % 16 == 0 || it + 1 == maxiter) {
@@ -263,7 +276,6 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
     }
     if (!rc) rc = check_cuda(cudaMemcpyAsync(h.data(), sc, sizeof(GfDet) * nd, cudaMemcpyDeviceToHost, st), "read");
     if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "gap filling");
-    cudaFree(y); cudaFree(r); cudaFree(p); cudaFree(q); cudaFree(sc); cudaFree(x32); cudaFree(n32);
     if (rc) return rc;
     all_done = true;
     for (int64_t i = 0; i < nd; ++i) {

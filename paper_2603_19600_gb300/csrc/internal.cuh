@@ -200,6 +200,11 @@ struct furax_noise {
     float2 *tw32 = nullptr;
     double *spec64 = nullptr;   // [ndet][8192]
     float *spec32 = nullptr;
+    // gap-filling workspaces (TOD-sized), allocated by the first furax_gapfill that needs them and
+    // reused by later calls; freed with the handle
+    double *gf_y = nullptr, *gf_r = nullptr, *gf_p = nullptr, *gf_q = nullptr;
+    float *gf_x32 = nullptr, *gf_n32 = nullptr;
+    void *gf_sc = nullptr;
     fx::NoiseView view() const { return fx::NoiseView{kind, ntaps, p64, p32, diag}; }
 };
 

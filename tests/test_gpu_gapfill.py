@@ -146,3 +146,24 @@ def test_gapfill_rejects_a_white_handle(fx, dev):
     with pytest.raises(fx.FuraxError) as e:
         fx._native.furax_gapfill(W.handle, 2, x, torch.ones_like(x, dtype=torch.uint8), x, out)
     assert e.value.code == -1
+
+
+def test_workspaces_are_reused_across_calls_and_precisions(fx, dev):
+    """The handle keeps the gap-filling workspaces: a repeated call reproduces the first bit for bit,
+    and switching precision on the same handle (which adds the FP64 band-product vector) changes
+    nothing for the FP32 call that follows."""
+    obs, cov, d, n, valid = make(64, 5)
+    P = fx.Pointing.from_observations(obs, mode="cache_f32", device=dev)
+    N = fx.Noise.banded(P, np.concatenate(cov))
+    dt = torch.as_tensor(cat(d), device=dev)
+    vt = torch.as_tensor(cat(valid), device=dev)
+    nt = torch.as_tensor(cat(n), device=dev)
+    kw = dict(maxiter=2000, tol=1e-10)
+    a, ia, oka = fx.gapfill(N, dt, vt, nt, precision="f32", **kw)
+    b, ib, okb = fx.gapfill(N, dt, vt, nt, precision="f32", **kw)
+    c, ic, okc = fx.gapfill(N, dt, vt, nt, precision="f64", **kw)
+    e, ie, oke = fx.gapfill(N, dt, vt, nt, precision="f32", **kw)
+    assert oka and okb and okc and oke
+    assert torch.equal(a, b) and torch.equal(a, e)
+    assert list(ia) == list(ib) == list(ie)
+    assert rel(a.cpu().numpy(), c.cpu().numpy()) < 1e-6
