@@ -66,7 +66,11 @@ __global__ void tpl_moments_kernel(int64_t ndet, NoiseView nv, int halo, double2
     mom[i] = make_double2(m0, m2);
 }
 
-// gram[det] += sum over the tile of P_k(tau_t) (W P_l)(t), k, l < 4 (FP64).
+// gram[det] += sum over the tile of P_k(tau_t) (W P_l)(t), k, l < 4 (FP64). Interior samples enter
+// through the power sums S_m = sum tau^m (m <= 6): there (W P_l) = mu0 P_l + k2 P_l'' with
+// k2 = mu2 h^2 / 2, so the entry is sum_{m,n} A_km (mu0 A_ln + k2 B_ln) S_{m+n} with A the
+// Legendre coefficients in powers of tau and B those of P_l''. Samples within a half-band of
+// either end are summed term by term.
 __global__ void __launch_bounds__(FT) tpl_gram_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
                                                       NoiseView nv, TplView tv, double *__restrict__ gram)
 {
@@ -74,23 +78,59 @@ __global__ void __launch_bounds__(FT) tpl_gram_kernel(const Tile *__restrict__ t
     const ObsInfo ob = obs[tl.obs];
     const int64_t gdet = ob.det_off + tl.det;
     const double h = ob.nsamp > 1 ? 2.0 / (double)(ob.nsamp - 1) : 0.0;
-    double g[16];
+    double S[7], g[16];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) S[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = 0.0;
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t t = tl.t0 + u;
-        double w[4], L[4];
-        wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
-        legendre4(tpl_tau<double>(t, ob.nsamp, h), L);
+        const double tau = tpl_tau<double>(t, ob.nsamp, h);
+        if (tpl_interior(tv, t, ob.nsamp)) {
+            double v = 1.0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+            for (int m = 0; m < 7; ++m) {
+                S[m] += v;
+                v *= tau;
+            }
+        } else {
+            double w[4], L[4];
+            wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
+            legendre4(tau, L);
 #pragma unroll
-            for (int l = 0; l < 4; ++l) g[4 * k + l] += L[k] * w[l];
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) g[4 * k + l] += L[k] * w[l];
+        }
     }
-    cta_sum<16, double>(g);
-    if (threadIdx.x == 0)
-        for (int i = 0; i < 16; ++i)
-            if ((i >> 2) <= tv.order && (i & 3) <= tv.order) red_add_f64(gram + 16 * gdet + i, g[i]);
+    const bool has_edge = tl.t0 < tv.halo || tl.t0 + tl.len + tv.halo > ob.nsamp;   // CTA-uniform
+    cta_sum<7, double>(S);
+    if (has_edge) cta_sum<16, double>(g);
+    if (threadIdx.x != 0) return;
+    constexpr double A[4][4] = {{1.0, 0.0, 0.0, 0.0}, {0.0, 1.0, 0.0, 0.0}, {-0.5, 0.0, 1.5, 0.0}, {0.0, -1.5, 0.0, 2.5}};
+    constexpr double B[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {3.0, 0.0}, {0.0, 15.0}};   // P_l'' = B_l0 + B_l1 tau
+    const double2 mo = tv.mom[gdet];
+    const double mu0 = mo.x, k2 = mo.y * h * h * 0.5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (k > tv.order || l > tv.order) continue;
+            double v = 0.0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (A[k][m] == 0.0) continue;
+                double c = 0.0;
+#pragma unroll
+                for (int n = 0; n < 4; ++n)
+                    if (A[l][n] != 0.0) c += mu0 * A[l][n] * S[m + n];
+#pragma unroll
+                for (int n = 0; n < 2; ++n)
+                    if (B[l][n] != 0.0) c += k2 * B[l][n] * S[m + n];
+                v += A[k][m] * c;
+            }
+            red_add_f64(gram + 16 * gdet + 4 * k + l, v + (has_edge ? g[4 * k + l] : 0.0));
+        }
 }
 
 // ginv[det] = G^-1 by Cholesky (K+1 <= 4, FP64). A pivot that loses all but 1e-13 of its
@@ -199,7 +239,9 @@ __global__ void __launch_bounds__(FT) tpl_project_kernel(const Tile *__restrict_
     }
     cta_sum<4, T>(acc);
     if (threadIdx.x == 0)
-        for (int l = 0; l <= tv.order; ++l) red_add_f64(a + 4 * gdet + l, scale * (double)acc[l]);
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            if (l <= tv.order) red_add_f64(a + 4 * gdet + l, scale * (double)acc[l]);
 }
 
 // a[det] += scale sum_t (W T)(t) d_t for FP32 data d, FP64-accurate on FP32 units. Interior samples
