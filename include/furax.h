@@ -334,9 +334,11 @@ furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void 
  * [nsamp_total] of dtype (out may be d); valid: device uint8 [nsamp_total], 1 = observed. n_real
  * is the unconstrained realisation (the caller's random draws). Per detector, CG from 0 until
  * ||r|| <= tol ||r_0|| or maxiter iterations; precision FURAX_F64 applies N in FP64, FURAX_F32 in
- * FP32 (vectors and scalars stay FP64; the filled values are then good to ~1e-7 relative);
+ * FP32 (vectors and scalars stay FP64; the filled values are then good to ~1e-7 relative),
+ * FURAX_PREC_F32X2 FP64-accurate in double-FP32 on the FP32 units (bands of up to 64 taps; a
+ * longer band is applied as for FURAX_F64);
  * iters_out: host int32 [sum ndet] or NULL. The first call allocates TOD-sized workspaces in the
- * handle (3 FP64, plus 1 FP64 for FURAX_F64 or 2 FP32 for FURAX_F32) that later calls reuse and
+ * handle (3 FP64, plus 1 FP64 for FURAX_F64 / FURAX_PREC_F32X2 or 2 FP32 for FURAX_F32) that later calls reuse and
  * furax_noise_destroy frees, so calls on one handle must not run concurrently; synchronises
  * stream. FURAX_ENOTCONVERGED when a detector stopped at maxiter (out is still written). */
 furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_t *valid, const void *n_real,

@@ -666,7 +666,7 @@ furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_
     REQUIRE(valid_dtype(dtype), "unknown dtype %d", dtype);
     REQUIRE(maxiter >= 0 && maxiter <= 1000000, "maxiter out of range");
     REQUIRE(tol >= 0.0, "tol must be >= 0");
-    REQUIRE(valid_dtype(precision), "unknown precision %d", precision);
+    REQUIRE(valid_dtype(precision) || precision == FURAX_PREC_F32X2, "unknown precision %d", precision);
     return gapfill(cov, d, valid, n_real, out, dtype, maxiter, tol, precision, iters_out, (cudaStream_t)stream);
 }
 

@@ -143,6 +143,65 @@ __global__ void __launch_bounds__(FT, 2) fused_df_kernel(const Tile *__restrict_
 }
 
 // ------------------------------------------------------------------------------------
+// Standalone N^-1 on an FP64 TOD, FP64-accurate on FP32 units: the input and the taps are split
+// into double-FP32 pairs and the band product is the compensated dot product above; the result
+// S + E is returned in FP64. For the band products of the FP64-accurate gap filling.
+// ------------------------------------------------------------------------------------
+template <bool BANDED>
+__global__ void __launch_bounds__(FT) ninv_df_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
+                                                     NoiseView nv, const double *__restrict__ in,
+                                                     double *__restrict__ out)
+{
+    __shared__ float xh[XS], xl[XS], th[MAXTAPS], tl[MAXTAPS];
+    const Tile tile = tiles[blockIdx.x];
+    const ObsInfo ob = obs[tile.obs];
+    const int64_t gdet = ob.det_off + tile.det;
+    const int64_t row = ob.tod_off + tile.det * ob.nsamp;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if (threadIdx.x < MAXTAPS) {
+        double c = 0.0;
+        if constexpr (BANDED) c = threadIdx.x < nv.ntaps ? nv.p64[gdet * nv.ntaps + threadIdx.x] : 0.0;
+        else c = threadIdx.x == 0 ? nv.p64[gdet] : 0.0;
+        split_df(c, th[threadIdx.x], tl[threadIdx.x]);
+    }
+    const int nload = tile.len + 2 * halo;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tile.t0 - halo + u;
+        split_df((t >= 0 && t < ob.nsamp) ? in[row + t] : 0.0, xh[spos(u)], xl[spos(u)]);
+    }
+    __syncthreads();
+    const int base = threadIdx.x * FR;
+    if (base >= tile.len) return;
+    float S[FR], E[FR];
+    if constexpr (BANDED) {
+        band_product_df<FR>(xh, xl, th, tl, base, S, E);
+    } else {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            S[r] = 0.f;
+            E[r] = 0.f;
+            dot2_step(th[0], tl[0], xh[spos(base + r)], xl[spos(base + r)], S[r], E[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < FR; ++r)
+        if (base + r < tile.len) out[row + tile.t0 + base + r] = (double)S[r] + (double)E[r];
+}
+
+furax_status launch_ninv_df(const furax_noise *n, const double *in, double *out, cudaStream_t st)
+{
+    if (long_band(n)) return set_error(FURAX_EINVAL, "internal: the double-FP32 N^-1 takes bands of up to %d taps", MAXTAPS);
+    if (n->n_tiles == 0) return FURAX_OK;
+    const unsigned g = (unsigned)n->n_tiles;
+    if (n->kind == FURAX_NOISE_BANDED)
+        ninv_df_kernel<true><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, n->view(), in, out);
+    else
+        ninv_df_kernel<false><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, n->view(), in, out);
+    count_launches(1);
+    return check_launch("double-FP32 N^-1 apply");
+}
+
+// ------------------------------------------------------------------------------------
 // Right-hand side from FP32 time-ordered data: acc64 + lo += P^T N^-1 d.
 // The input word is exact in FP32, so the compensated band product carries no input low word.
 // The output y = S + E is renormalised to (y_hi, y_lo); each weighted term y w (w = 1, cos, sin)

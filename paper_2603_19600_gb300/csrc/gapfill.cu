@@ -188,6 +188,12 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
                      int maxiter, double tol, int precision, int32_t *iters_out, cudaStream_t st)
 {
     const bool f32 = precision == FURAX_F32;   // band product in FP32, vectors and scalars in FP64
+    // FURAX_PREC_F32X2: the FP64 path with its band products in double-FP32 (short bands; a long
+    // band keeps the FP64 overlap-save product)
+    const bool df = precision == FURAX_PREC_F32X2 && !long_band(n);
+    auto ninv64 = [&](const double *in, double *o) {
+        return df ? launch_ninv_df(n, in, o, st) : launch_ninv(n, in, o, FURAX_F64, st);
+    };
     const int64_t ns = n->nsamp_total, nd = n->ndet_total;
     if (ns == 0 || nd == 0) return FURAX_OK;
     const unsigned g = (unsigned)n->n_tiles;
@@ -234,7 +240,7 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
             gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
             gf_update_kernel<float><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, n32, y, r, sc);
         } else {
-            if ((rc = launch_ninv(n, p, q, FURAX_F64, st))) break;
+            if ((rc = ninv64(p, q))) break;
             gf_pq_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, q, sc);
             gf_alpha_kernel<<<dg, 128, 0, st>>>(nd, sc);
             gf_update_kernel<double><<<g, FT, 0, st>>>(n->d_tiles, n->d_obs, valid, p, q, y, r, sc);
@@ -256,7 +262,7 @@ furax_status gapfill(const furax_noise *n, const void *d, const uint8_t *valid, 
         count_launches(1);
         rc = launch_ninv(n, x32, n32, FURAX_F32, st);
     } else if (!rc) {
-        rc = launch_ninv(n, y, q, FURAX_F64, st);
+        rc = ninv64(y, q);
     }
     if (!rc) {
         if (dtype == FURAX_F64 && f32)

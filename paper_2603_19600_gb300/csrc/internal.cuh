@@ -228,6 +228,8 @@ furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rco
 
 // ---- launchers (noise.cu)
 furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st);
+// FP64 in, FP64 out, band product in double-FP32 (bands of up to MAXTAPS taps; fused_df.cu)
+furax_status launch_ninv_df(const furax_noise *n, const double *in, double *out, cudaStream_t st);
 // Bands longer than the fused kernels hold go through the TOD in HBM (overlap-save N^-1).
 inline bool long_band(const furax_noise *n) { return n->kind == FURAX_NOISE_BANDED && n->ntaps > MAXTAPS; }
 // noise_fft.cu: blocks, twiddles and spectra of a long band (synchronises st); the N^-1 apply.

@@ -207,7 +207,8 @@ class Templates:
 def gapfill(cov: Noise, d, valid, n_real, maxiter=1000, tol=1e-10, out=None, precision="f64"):
     """Fill the gaps (valid == 0) of the TOD d with the constrained realisation
     n_g + N_gv N_vv^-1 (d_v - n_v); cov is a banded Noise whose taps hold the covariance band N,
-    n_real a realisation of covariance N; precision "f32" applies N in FP32. The TOD-sized
+    n_real a realisation of covariance N; precision "f32" applies N in FP32, "f32x2" FP64-accurate
+    in double-FP32 on the FP32 units (bands of up to 64 taps), "f64" in FP64. The TOD-sized
     workspaces stay in cov for later calls. Returns (filled TOD, per-detector iterations,
     converged)."""
     if cov.kind != "banded":

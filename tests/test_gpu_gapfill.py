@@ -41,7 +41,8 @@ def cat(xs):
 
 @pytest.mark.parametrize("ntaps", [64, 300])
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-8), (torch.float32, 2e-6)])
-def test_gapfill_matches_oracle(fx, dev, ntaps, dtype, tol):
+@pytest.mark.parametrize("precision", ["f64", "f32x2"])   # f32x2: double-FP32 band products (64 taps)
+def test_gapfill_matches_oracle(fx, dev, ntaps, dtype, tol, precision):
     obs, cov, d, n, valid = make(ntaps, ntaps)
     if dtype == torch.float32:
         d = [x.astype(np.float32).astype(np.float64) for x in d]
@@ -51,7 +52,7 @@ def test_gapfill_matches_oracle(fx, dev, ntaps, dtype, tol):
     dt = torch.as_tensor(cat(d), device=dev, dtype=dtype)
     out, iters, ok = fx.gapfill(N, dt, torch.as_tensor(cat(valid), device=dev), torch.as_tensor(cat(n), device=dev,
                                                                                                dtype=dtype),
-                                maxiter=2000, tol=1e-12)
+                                maxiter=2000, tol=1e-12, precision=precision)
     assert ok
     got = out.double().cpu().numpy()
     off = 0
