@@ -113,16 +113,20 @@ def test_ptfp_apply_matches_oracle(fx, dev, orc, batch, mode, prec, acc, tol):
 
 
 @pytest.mark.parametrize("order", [0, 1, 3])
-@pytest.mark.parametrize("kind", ["banded", "white"])
+@pytest.mark.parametrize("kind", ["banded", "white", "long"])
 @pytest.mark.parametrize("precision,mode", [("f32", "cache_mixed"), ("f32", "on_the_fly"), ("f64", "cache_f64")])
 def test_deprojected_rhs_matches_oracle(fx, dev, orc, batch, order, kind, precision, mode):
     """The deprojected right-hand side S P^T F_T d of FP32 data, seen through the binned map
     M^-1 b. The mixed solver subtracts (W T) b inside its double-FP32 pass over d (a cubic per
-    tile in the interior, term by term at the stream ends); the FP64 solver in a pass of its own.
-    Large drifts along every Legendre degree make the correction the dominant term."""
+    tile in the interior, term by term at the stream ends); the FP64 solver, and any solver with a
+    long (overlap-save) band, in a pass of its own. Large drifts along every Legendre degree make
+    the correction the dominant term."""
     obs, taps, pts = batch
     P = fx.Pointing.from_observations(obs, mode=mode, device=dev)
-    if kind == "banded":
+    if kind in ("banded", "long"):
+        if kind == "long":   # 300 taps: streams of 40 and 200 samples lie wholly within a half-band of an end
+            taps = [np.tile(synth.inverse_noise_taps(300), (o.ndet, 1)) * (1.0 + 0.2 * np.arange(o.ndet))[:, None]
+                    for o in obs]
         N = fx.Noise.banded(P, np.concatenate(taps))
         on = [orc.Noise(taps=t) for t in taps]
     else:
