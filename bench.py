@@ -55,6 +55,8 @@ def parse():
                     help="time only the 1024-tap overlap-save N^-1 and its normal operator (profiling runs)")
     ap.add_argument("--deproject-only", action="store_true",
                     help="time only the template-deprojected solver step (profiling runs; not a bench line)")
+    ap.add_argument("--gap-fill-only", action="store_true",
+                    help="time only the gap filling, FP32 and double-FP32 band products (profiling runs)")
     ap.add_argument("--ndet", type=int, default=None, help="override the detector count (profiling runs)")
     ap.add_argument("--nsamp", type=int, default=None, help="override the samples per detector (profiling runs)")
     ap.add_argument("--nside", type=int, default=None, help="override nside (profiling runs)")
@@ -596,6 +598,11 @@ def main():
     if args.deproject_only:
         r = deproject_step(fx, dev, stream, wl, q_bore, q_det, d, taps, steps=max(1, args.steps))
         print(json.dumps({"deproject_only": True, **wl, **r}), flush=True)
+        return
+
+    if args.gap_fill_only:
+        r = gap_fill(fx, dev, stream, wl, q_bore, q_det, d, reps=max(1, args.steps))
+        print(json.dumps({"gap_fill_only": True, **wl, **r}), flush=True)
         return
 
     def step(d_ready=None):
