@@ -3,6 +3,7 @@
 // when |a| >= |b|) and the FMA-based exact product; each operation is written with explicit
 // round-to-nearest intrinsics so that the compiler cannot contract or reassociate it.
 #pragma once
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace fx {
@@ -50,6 +51,39 @@ __device__ __forceinline__ void df_horner(float &h, float &l, float j, float eh,
     h = p;
     l = pl;
     df_add(h, l, eh, el);
+}
+
+// binary32 -> binary64 from the IEEE 754 encodings: sign kept, exponent rebiased by
+// 1023 - 127 = 896, significand shifted into the top of the 52-bit field. Exact for normal
+// numbers and zeros; subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63));
+        return (double)f;
+    }
+    const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// binary64 -> binary32 rounded to nearest even, from the encodings: for results in binary32's
+// normal range the exponent is rebiased by -896 and the 52-bit significand cut to 23 bits, adding
+// one unit when the 29 dropped bits exceed half a unit or equal it with an odd kept part (a carry
+// into the exponent is the correct rounded value, up to infinity). Other inputs (zeros,
+// binary32 subnormal results, overflow, infinities, NaNs) take the hardware conversion. Used where
+// FP64 conversions would occupy the FP64 pipe, which on this GPU is the bottleneck.
+__device__ __forceinline__ float f64_to_f32_bits(double v)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+    if (e < 897u || e > 1150u) return (float)v;
+    const uint64_t m = b & 0xfffffffffffffull;
+    uint32_t r = ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint64_t rem = m & 0x1fffffffull, half = 0x10000000ull;
+    if (rem > half || (rem == half && (r & 1u))) r += 1u;
+    return __uint_as_float((uint32_t)(b >> 63) << 31 | r);
 }
 
 }  // namespace fx

@@ -325,21 +325,6 @@ __device__ __forceinline__ void band_product_dfx2(const float *__restrict__ xs, 
     }
 }
 
-// binary32 -> binary64 from the IEEE 754 encodings: sign kept, exponent rebiased by
-// 1023 - 127 = 896, significand shifted into the top of the 52-bit field. Exact for normal
-// numbers and zeros; subnormals, infinities and NaNs take the hardware conversion.
-__device__ __forceinline__ double f32_to_f64_bits(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) {
-        if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63));
-        return (double)f;
-    }
-    const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)d);
-}
-
 // Pixel and weights of one sample as double-FP32 pairs (offset rotation included).
 template <int MODE>
 __device__ __forceinline__ int32_t sample_df(const PointingView &pv, const ObsInfo &ob, int32_t det, int64_t t,

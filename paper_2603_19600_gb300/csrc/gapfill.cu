@@ -8,6 +8,7 @@
 // band product (direct, or overlap-save for long bands) between two applications of the mask,
 // and each detector keeps its own scalars (per-CTA partial sums reduced into them).
 #include "tile.cuh"
+#include "dfloat.cuh"
 
 namespace fx {
 
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(FT) gf_to_f32_kernel(const Tile *__restrict__ 
     const ObsInfo ob = obs[tl.obs];
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
-        x32[i] = (float)x[i];
+        x32[i] = f64_to_f32_bits(x[i]);
     }
 }
 
@@ -95,7 +96,11 @@ __global__ void __launch_bounds__(FT) gf_pq_kernel(const Tile *__restrict__ tile
     double acc = 0.0;
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t i = tod_index(ob, tl, u);
-        const double qv = valid[i] ? (double)nq[i] : 0.0;
+        double qv = 0.0;
+        if (valid[i]) {
+            if constexpr (sizeof(QT) == 8) qv = nq[i];
+            else qv = f32_to_f64_bits(nq[i]);   // exact, and no FP64 conversion issued
+        }
         if constexpr (sizeof(QT) == 8) q[i] = qv;
         acc += p[i] * qv;
     }
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(FT) gf_update_kernel(const Tile *__restrict__ 
         y[i] += s.alpha * p[i];
         double qv;
         if constexpr (sizeof(QT) == 8) qv = q[i];
-        else qv = valid[i] ? (double)q[i] : 0.0;
+        else qv = valid[i] ? f32_to_f64_bits(q[i]) : 0.0;
         const double rv = r[i] - s.alpha * qv;
         r[i] = rv;
         acc += rv * rv;
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ til
         const int64_t i = tod_index(ob, tl, u);
         const double pv = r[i] + s.beta * p[i];
         p[i] = pv;
-        if (x32) x32[i] = (float)pv;
+        if (x32) x32[i] = f64_to_f32_bits(pv);
     }
 }
 
