@@ -367,6 +367,50 @@ furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, 
  * furax_mapmaker_cg checks this itself at its synchronisation points. */
 furax_status furax_device_status(furax_pointing_t *p, void *stream);
 
+/* Budget of every bounded device-side wait of this handle's pipelined kernels (the mbarrier
+ * hand-offs between the roles of the cached FP32 operator), in SM clock cycles; 0 restores the
+ * default of 2^32 cycles (about 2 s). A wait that runs out sets the error word that
+ * furax_device_status reports (FURAX_ETIMEOUT) and its role leaves its loop, so the kernel
+ * returns; the output of that launch is then incomplete. Ordered on `stream`; synchronises it.
+ * Errors: FURAX_EINVAL for a NULL handle or a negative budget. The paper has no counterpart:
+ * this is a property of the GPU pipeline. */
+furax_status furax_set_wait_budget(furax_pointing_t *p, int64_t cycles, void *stream);
+
+/* Test hook for the bounded waits: with hold != 0 the loader role of the cached FP32 operator
+ * issues no copies in this handle's later launches, so the other roles' waits run out after the
+ * wait budget (no copy is ever left in flight). hold = 0 restores normal operation. Ordered on
+ * `stream`; synchronises it. The paper has no counterpart. */
+furax_status furax_debug_hold_loader(furax_pointing_t *p, int32_t hold, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Device probes (measurement instruments; the paper has no counterpart). They give the
+ * per-unit rates of this GPU that bound the kernels that are not HBM-bound, for their roofline
+ * fractions, and check the encoding-level FP32/FP64 conversions against the hardware ones.
+ * ------------------------------------------------------------------------------------- */
+
+/* out32[i] = in64[i] rounded to binary32 (nearest even) and out64[i] = in32[i] widened, both by
+ * the library's own encoding arithmetic (the conversions the gap-filling vector passes and the
+ * FP64 accumulation of the double-FP32 path use). Either pair may be NULL. Device arrays of n
+ * elements; asynchronous on `stream`. FURAX_EINVAL for n < 0 or an input without its output. */
+furax_status furax_probe_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n,
+                                 void *stream);
+
+/* Launch one FMA throughput kernel (kind 0: FP64 FMA, 1: FP32 FMA, 2: packed FP32x2 FMA) that
+ * issues `iters` iterations of 8 independent chains per thread on 8 x 256 threads per SM;
+ * *flops receives the kernel's floating-point operation count (2 per FMA). The caller times the
+ * launch on `stream` with events. sink: device scratch of one element (never written in
+ * practice). FURAX_EINVAL for a bad kind, iters < 1 or NULL pointers. */
+furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink, double *flops, void *stream);
+
+/* Random L2 operations at the n device indices idx[i] (each in [0, ntable)): kind 0 gathers a
+ * float4 from table (ntable float4), 1 issues one red.add.v4.f32 into it, 2 the compensated
+ * pair of FURAX_ACC_F32_KAHAN (atomic add returning the old value + a reduction of its rounding
+ * error into table[ntable + idx], so table holds 2 ntable float4), 3 three FP64 reductions
+ * (table holds [ntable][3] doubles). Grid of 8 x 256 threads per SM; the caller times it. The
+ * indices are not checked on the device. sink: one float of device scratch. */
+furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable, void *sink,
+                            void *stream);
+
 /* Thread-local message describing the last error ("" if none). Never NULL. */
 const char *furax_last_error(void);
 /* Number of kernels this library has launched in this process (graph replays count their

@@ -60,6 +60,11 @@ _SIGS = {
     "furax_pointing_refresh": [_V, _V],
     "furax_pointing_cache": [_V, _V, _V, _V, _V],
     "furax_device_status": [_V, _V],
+    "furax_set_wait_budget": [_V, _I64, _V],
+    "furax_probe_convert": [_V, _V, _V, _V, _I64, _V],
+    "furax_probe_fma": [_I32, _I64, _V, ctypes.POINTER(_D), _V],
+    "furax_probe_l2": [_I32, _V, _I64, _V, _I64, _V, _V],
+    "furax_debug_hold_loader": [_V, _I32, _V],
     "furax_pointing_set_psi_offset": [_V, _V, _V],
     "furax_profile_read": [_I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)],
     "furax_pointing_expand": [_V, _V, _V, _V, _I32, _V],
@@ -210,6 +215,41 @@ def furax_pointing_refresh(h, stream=None) -> None:
 def furax_device_status(h, stream=None) -> None:
     """Raise FuraxError (FURAX_ETIMEOUT) if a bounded device-side wait gave up."""
     _call("furax_device_status", h, _stream(stream))
+
+
+def furax_set_wait_budget(h, cycles: int, stream=None) -> None:
+    """Budget (SM cycles) of the handle's bounded device waits; 0 restores the default."""
+    _call("furax_set_wait_budget", h, int(cycles), _stream(stream))
+
+
+def furax_debug_hold_loader(h, hold: bool, stream=None) -> None:
+    """Test hook: hold the cached FP32 operator's loader so that its other roles' waits run out."""
+    _call("furax_debug_hold_loader", h, int(bool(hold)), _stream(stream))
+
+
+def furax_probe_convert(in64=None, out32=None, in32=None, out64=None, stream=None) -> None:
+    """Encoding-level conversions: out32 = binary32(in64) (nearest even), out64 = binary64(in32)."""
+    n = (in64 if in64 is not None else in32).numel()
+    _call("furax_probe_convert", _ptr(in64, torch.float64, n, "in64"), _ptr(out32, torch.float32, n, "out32"),
+          _ptr(in32, torch.float32, n, "in32"), _ptr(out64, torch.float64, n, "out64"), n, _stream(stream))
+
+
+def furax_probe_fma(kind: int, iters: int, sink, stream=None) -> float:
+    """Launch the FMA throughput probe (0 FP64, 1 FP32, 2 packed FP32); returns its flop count."""
+    fl = _D()
+    _call("furax_probe_fma", int(kind), int(iters), _ptr(sink, None, None, "sink"), ctypes.byref(fl), _stream(stream))
+    return fl.value
+
+
+def furax_probe_l2(kind: int, idx, table, ntable: int, sink, stream=None) -> None:
+    """Random L2 operations at idx (int32, each in [0, ntable)) on table (see furax.h for its size)."""
+    if idx.numel() and (int(idx.min()) < 0 or int(idx.max()) >= ntable):
+        raise ValueError("probe indices must lie in [0, ntable)")
+    need = {0: 16 * ntable, 1: 16 * ntable, 2: 32 * ntable, 3: 24 * ntable}[int(kind)]
+    if table.numel() * table.element_size() < need:
+        raise ValueError(f"probe table needs {need} bytes")
+    _call("furax_probe_l2", int(kind), _ptr(idx, torch.int32, None, "idx"), idx.numel(), _ptr(table, None, None, "table"),
+          int(ntable), _ptr(sink, None, None, "sink"), _stream(stream))
 
 
 def furax_profile_enable(on: bool) -> None:

@@ -229,6 +229,26 @@ furax_status furax_device_status(furax_pointing_t *p, void *stream)
     return FURAX_OK;
 }
 
+furax_status furax_set_wait_budget(furax_pointing_t *p, int64_t cycles, void *stream)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    REQUIRE(cycles >= 0, "the wait budget must be >= 0 cycles (0 selects the default)");
+    cudaStream_t st = (cudaStream_t)stream;
+    // a kernel reads the budget at its start: the write is ordered on the stream like a launch
+    furax_status rc = check_cuda(cudaMemcpyAsync(p->d_err + 2, &cycles, sizeof cycles, cudaMemcpyHostToDevice, st),
+                                 "set wait budget");
+    return rc ? rc : check_cuda(cudaStreamSynchronize(st), "wait budget sync");
+}
+
+furax_status furax_debug_hold_loader(furax_pointing_t *p, int32_t hold, void *stream)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned h = hold ? 1u : 0u;
+    furax_status rc = check_cuda(cudaMemcpyAsync(p->d_err + 1, &h, sizeof h, cudaMemcpyHostToDevice, st), "hold loader");
+    return rc ? rc : check_cuda(cudaStreamSynchronize(st), "hold loader sync");
+}
+
 furax_status furax_pointing_cache(const furax_pointing_t *p, int32_t *pix, float *c, float *s, void *stream)
 {
     REQUIRE(p, "pointing handle is NULL");
@@ -342,8 +362,8 @@ furax_status furax_pointing_create(const furax_obs_desc *desc, int32_t mode, voi
         (rc = up((void **)&p->d_tiles, p->tiles.data(), sizeof(Tile) * p->tiles.size())) ||
         (rc = up((void **)&p->d_ptiles, p->ptiles.data(), sizeof(PTile) * p->ptiles.size())) ||
         (rc = ensure_ws(p, (void **)&p->d_psi_cs, sizeof(double2) * det)) ||
-        (rc = ensure_ws(p, (void **)&p->d_err, sizeof(unsigned))) ||
-        (rc = check_cuda(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), st), "memset"))) {
+        (rc = ensure_ws(p, (void **)&p->d_err, sizeof(unsigned) * kCtlWords)) ||
+        (rc = check_cuda(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned) * kCtlWords, st), "memset"))) {
         pointing_free(p);
         return rc;
     }

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     TmaSmem &S = *reinterpret_cast<TmaSmem *>(tsm);
     constexpr int halo = BANDED ? kHalo : 0;
     const int warp = threadIdx.x >> 5;
+    const long long budget = wait_budget(err);
     if (threadIdx.x == 0) {
         for (int i = 0; i < kRawStages; ++i) { mbar_init(&S.raw_full[i], 1); mbar_init(&S.raw_empty[i], 32 * kTmaConsumer); }
         for (int i = 0; i < kXsStages; ++i) { mbar_init(&S.xs_full[i], 32 * kTmaGather); mbar_init(&S.xs_empty[i], 32 * kTmaConsumer); }
@@ -136,11 +137,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     if (warp == kTmaGather + kTmaConsumer) {
         // ---------------- loader
         if ((threadIdx.x & 31) != 0) return;
+        // held (test hook): issue nothing; the gather and consumer waits then run out
+        if (loader_held(err)) return;
         int64_t it = 0;
         for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
             const int r = (int)(it % kRawStages);
             const uint32_t par = (uint32_t)((it / kRawStages) & 1);
-            if (!mbar_wait(&S.raw_empty[r], par ^ 1u, err)) break;
+            if (!mbar_wait(&S.raw_empty[r], par ^ 1u, err, budget)) break;
             const Tile tl = tiles[ti];
             const ObsInfo ob = pv.obs[tl.obs];
             const TileSpan sp = tile_span(tl, ob, halo);
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         // Copies into a stage complete its current phase; wait for the last one issued into each
         // stage so that no copy is still writing when the CTA exits.
         for (int64_t j = it - 1; j >= 0 && j >= it - kRawStages; --j)
-            mbar_wait(&S.raw_full[j % kRawStages], (uint32_t)((j / kRawStages) & 1), err);
+            mbar_wait(&S.raw_full[j % kRawStages], (uint32_t)((j / kRawStages) & 1), err, budget);
         return;
     }
 
@@ -167,8 +170,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
             const int r = (int)(it % kRawStages);
             const int q = (int)(it % kXsStages);
-            if (!mbar_wait(&S.xs_empty[q], (uint32_t)(((it / kXsStages) & 1) ^ 1), err)) break;
-            if (!mbar_wait(&S.raw_full[r], (uint32_t)((it / kRawStages) & 1), err)) break;
+            if (!mbar_wait(&S.xs_empty[q], (uint32_t)(((it / kXsStages) & 1) ^ 1), err, budget)) break;
+            if (!mbar_wait(&S.raw_full[r], (uint32_t)((it / kRawStages) & 1), err, budget)) break;
             const Tile tl = tiles[ti];
             const ObsInfo ob = pv.obs[tl.obs];
             const int64_t gdet = ob.det_off + tl.det;
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
         const int r = (int)(it % kRawStages);
         const int q = (int)(it % kXsStages);
-        const bool ok = mbar_wait(&S.xs_full[q], (uint32_t)((it / kXsStages) & 1), err);
+        const bool ok = mbar_wait(&S.xs_full[q], (uint32_t)((it / kXsStages) & 1), err, budget);
         const Tile tl = tiles[ti];
         const ObsInfo ob = pv.obs[tl.obs];
         const int64_t gdet = ob.det_off + tl.det;

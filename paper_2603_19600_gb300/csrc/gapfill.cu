@@ -174,12 +174,13 @@ __global__ void __launch_bounds__(FT) gf_dir_kernel(const Tile *__restrict__ til
     }
 }
 
-// out = d on observed samples, n + (N y) in the gaps.
+// out = d on observed samples, n + (N y) in the gaps. out may be d (documented in-place use), so
+// neither carries __restrict__.
 template <typename DT, typename QT>
 __global__ void __launch_bounds__(FT) gf_fill_kernel(const Tile *__restrict__ tiles, const ObsInfo *__restrict__ obs,
-                                                     const DT *__restrict__ d, const DT *__restrict__ nr,
+                                                     const DT *d, const DT *__restrict__ nr,
                                                      const uint8_t *__restrict__ valid, const QT *__restrict__ ny,
-                                                     DT *__restrict__ out)
+                                                     DT *out)
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];

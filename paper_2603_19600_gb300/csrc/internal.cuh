@@ -15,6 +15,7 @@ constexpr int TILE = 4096;      // samples per work tile (one detector, contiguo
 constexpr int PTILE = 4096;     // pixels per pixel tile (vector kernels, per-observation reductions)
 constexpr int MAXTAPS = 64;     // longest band of the fused kernels (c_0..c_63)
 constexpr int kLongTaps = 2048; // longest band of the overlap-save N^-1 (TOD in HBM)
+constexpr int kCtlWords = 4;    // device control block of a pointing handle (error, hold, wait budget)
 
 struct ObsInfo {
     int64_t nsamp;     // samples per detector
@@ -143,7 +144,8 @@ struct furax_pointing {
     int64_t nsamp_total = 0, npix_total = 0, ndet_total = 0, nbore_total = 0, n_invalid = 0;
     int32_t max_ndet = 0;
     int32_t n_sm = 1;                 // SMs of the device (persistent grids)
-    unsigned *d_err = nullptr;        // device error word: bounded waits that gave up
+    unsigned *d_err = nullptr;        // device control block (kCtlWords): error word of the bounded waits,
+                                      // loader hold flag, wait budget (mbarrier.cuh)
     // workspaces, allocated on first use and freed by destroy
     float4 *ws_map32 = nullptr;       // [npix] padded FP32 copy of a map for the gather
     float4 *ws_acc_hi = nullptr;      // [npix] FP32 accumulator (I,Q,U,-)

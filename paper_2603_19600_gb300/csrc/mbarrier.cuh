@@ -1,6 +1,12 @@
 // Shared-memory mbarriers with bounded waits (producer/consumer hand-off inside one CTA).
-// A wait that has not completed after kWaitCycles SM cycles records an error word in global
+// A wait that has not completed within its budget of SM cycles records an error word in global
 // memory and returns false; the caller then leaves its loop, so a kernel always terminates.
+//
+// The handle's device control block (kCtlWords 32-bit words, furax_pointing::d_err):
+//   [0]    error word (kErrWaitTimeout once a wait gave up; cleared by furax_device_status)
+//   [1]    hold flag: the loader of the cached FP32 operator issues no copies while it is set
+//          (furax_debug_hold_loader), so that the other roles' waits run out
+//   [2..3] wait budget in SM cycles (int64; 0 selects kWaitCycles)
 #pragma once
 #include <cstdint>
 
@@ -8,6 +14,18 @@ namespace fx {
 
 constexpr long long kWaitCycles = 1LL << 32;   // ~2 s at 2 GHz: far above any legitimate wait
 constexpr unsigned kErrWaitTimeout = 1u;
+
+// The budget a kernel's waits use, read once at kernel start.
+__device__ __forceinline__ long long wait_budget(const unsigned *ctl)
+{
+    const long long b = *reinterpret_cast<const volatile long long *>(ctl + 2);
+    return b > 0 ? b : kWaitCycles;
+}
+
+__device__ __forceinline__ bool loader_held(const unsigned *ctl)
+{
+    return *reinterpret_cast<const volatile unsigned *>(ctl + 1) != 0u;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -35,13 +53,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait until the phase with the given parity has completed (acquire). Bounded.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err)
+// Wait until the phase with the given parity has completed (acquire). Bounded by `budget` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, long long budget)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             atomicOr(err, kErrWaitTimeout);
             return false;
         }

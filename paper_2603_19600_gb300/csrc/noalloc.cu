@@ -110,11 +110,13 @@ __global__ void noalloc_finalize_kernel(const float4 *__restrict__ scratch, cons
     }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-static furax_status noalloc_scratch(float4 **out)
+// Device address of the scratch array on the current device and the device's SM count, looked
+// up once per device (neither lookup allocates).
+static furax_status noalloc_scratch(float4 **out, int *n_sm)
 {
     static std::mutex mu;
     static float4 *addr[kNoAllocMaxDevices] = {};
+    static int sms[kNoAllocMaxDevices] = {};
     int dev = 0;
     furax_status rc = check_cuda(cudaGetDevice(&dev), "current device");
     if (rc) return rc;
@@ -122,10 +124,14 @@ static furax_status noalloc_scratch(float4 **out)
     std::lock_guard<std::mutex> lk(mu);
     if (!addr[dev]) {
         void *p = nullptr;
+        int n = 0;
         if ((rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "scratch symbol address"))) return rc;
+        if ((rc = check_cuda(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return rc;
+        sms[dev] = n > 0 ? n : 1;
         addr[dev] = static_cast<float4 *>(p);
     }
     *out = addr[dev];
+    *n_sm = sms[dev];
     return FURAX_OK;
 }
 
@@ -150,10 +156,12 @@ extern "C" furax_status furax_ptnp_apply_noalloc(const int32_t *pix, const float
     const int64_t nchunk = (nsamp + TILE - 1) / TILE;
     if (nchunk * ndet >= (1LL << 31)) return set_error(FURAX_EINVAL, "problem too large for one launch grid");
     float4 *scratch = nullptr;
-    furax_status rc = noalloc_scratch(&scratch);
+    int n_sm = 1;
+    furax_status rc = noalloc_scratch(&scratch, &n_sm);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned vg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((npix + 255) / 256, 152 * 8));
+    // grid-stride vector passes: eight 256-thread blocks per SM at most
+    const unsigned vg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((npix + 255) / 256, 8LL * n_sm));
     noalloc_pack_kernel<<<vg, 256, 0, st>>>(x, valid, scratch, npix);
     noalloc_tile_kernel<<<(unsigned)(nchunk * ndet), NT, 0, st>>>(pix, c, s, ndet, nsamp, npix, taps, ntaps, scratch);
     noalloc_finalize_kernel<<<vg, 256, 0, st>>>(scratch, valid, out, npix);

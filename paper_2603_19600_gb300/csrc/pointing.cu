@@ -92,7 +92,7 @@ furax_status launch_set_hwp(furax_pointing *p, const double *hwp, cudaStream_t s
     if (!hwp) { p->has_hwp = false; return FURAX_OK; }
     furax_status rc = ensure_ws(p, (void **)&p->d_hwp_cs, sizeof(double2) * std::max<int64_t>(1, p->nbore_total));
     if (rc) return rc;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 152 * 16));
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 16LL * p->n_sm));
     hwp_kernel<<<g, 256, 0, st>>>(hwp, p->d_hwp_cs, p->nbore_total);
     count_launches(1);
     p->has_hwp = true;
@@ -272,7 +272,7 @@ furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void
         count_launches(1);
         if ((rc = check_launch("pointing transpose"))) return rc;
     }
-    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 16);
+    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 16LL * p->n_sm);
     if (map_t == FURAX_F64)
         PT_finalize_kernel<double><<<fg, 256, 0, st>>>(acc, hi, lo, a64, (double *)map, np, accumulate);
     else
@@ -395,7 +395,7 @@ furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rco
         count_launches(1);
         if ((rc = check_launch("preconditioner accumulation"))) return rc;
     }
-    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 16);
+    const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 16LL * p->n_sm);
     bj_invert_kernel<<<fg, 256, 0, st>>>(blocks_inv, h, valid, rcond, np, rcond_min);
     count_launches(1);
     return check_launch("preconditioner inversion");

@@ -224,7 +224,7 @@ furax_status launch_expand_fast(const furax_pointing *p, unsigned long long *n_i
     furax_status rc;
     if ((rc = ensure_ws(pm, (void **)&pm->ws_bore_m, sizeof(float) * 18 * std::max<int64_t>(1, p->nbore_total))))
         return rc;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 152 * 16));
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 16LL * p->n_sm));
     bore_matrix_kernel<<<g, 256, 0, st>>>(p->q_bore, p->nbore_total, pm->ws_bore_m);
     count_launches(1);
     if ((rc = check_launch("boresight matrices"))) return rc;

@@ -129,12 +129,16 @@ __global__ void mask_copy_kernel(const double *__restrict__ x, const uint8_t *__
     }
 }
 
-static unsigned vgrid(int64_t np) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + VT - 1) / VT, 152 * 8)); }
+// Grid-stride vector kernels: at most eight VT-thread blocks per SM of the handle's device.
+static unsigned vgrid(const furax_pointing *p, int64_t np)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + VT - 1) / VT, 8LL * p->n_sm));
+}
 
 furax_status launch_pack_x32(const furax_pointing *p, const double *x, const uint8_t *valid, float4 *x32, float4 *za,
                              float4 *zb, cudaStream_t st)
 {
-    pack_x32_kernel<<<vgrid(p->npix_total), VT, 0, st>>>(x, valid, x32, za, zb, p->npix_total);
+    pack_x32_kernel<<<vgrid(p, p->npix_total), VT, 0, st>>>(x, valid, x32, za, zb, p->npix_total);
     count_launches(1);
     return check_launch("pack FP32 map");
 }
@@ -142,7 +146,7 @@ furax_status launch_pack_x32(const furax_pointing *p, const double *x, const uin
 furax_status launch_finalize_acc(const furax_pointing *p, int acc, const float4 *hi, const float4 *lo,
                                  const double *a64, const uint8_t *valid, double *out, cudaStream_t st)
 {
-    finalize_acc_kernel<<<vgrid(p->npix_total), VT, 0, st>>>(acc, hi, lo, a64, valid, out, p->npix_total);
+    finalize_acc_kernel<<<vgrid(p, p->npix_total), VT, 0, st>>>(acc, hi, lo, a64, valid, out, p->npix_total);
     count_launches(1);
     return check_launch("finalise accumulator");
 }
@@ -150,7 +154,7 @@ furax_status launch_finalize_acc(const furax_pointing *p, int acc, const float4 
 furax_status launch_mask_copy(const furax_pointing *p, const double *x, const uint8_t *valid, double *out,
                               cudaStream_t st)
 {
-    mask_copy_kernel<<<vgrid(p->npix_total), VT, 0, st>>>(x, valid, out, p->npix_total);
+    mask_copy_kernel<<<vgrid(p, p->npix_total), VT, 0, st>>>(x, valid, out, p->npix_total);
     count_launches(1);
     return check_launch("mask copy");
 }
@@ -185,7 +189,7 @@ furax_status launch_rhs_chain(const furax_pointing *p, const furax_noise *n, con
     furax_status rc;
     const void *d64 = d;
     if (d_t == FURAX_F32) {
-        tod_to_f64_kernel<<<vgrid(p->nsamp_total), VT, 0, st>>>((const float *)d, (double *)p->ws_tod, p->nsamp_total);
+        tod_to_f64_kernel<<<vgrid(p, p->nsamp_total), VT, 0, st>>>((const float *)d, (double *)p->ws_tod, p->nsamp_total);
         count_launches(1);
         if ((rc = check_launch("TOD to FP64"))) return rc;
         d64 = p->ws_tod;
@@ -614,7 +618,7 @@ static furax_status body_prologue(const Body &b, cudaStream_t st)
     CgWs *w = b.w;
     const bool f32 = b.precision != FURAX_F64;
     const int acc = f32 ? b.acc : FURAX_ACC_F64;
-    cg_pack_kernel<<<vgrid(b.np_cg), VT, 0, st>>>(w->p, f32 ? w->p32 : nullptr,
+    cg_pack_kernel<<<vgrid(b.p, b.np_cg), VT, 0, st>>>(w->p, f32 ? w->p32 : nullptr,
                                                           (f32 && acc != FURAX_ACC_F64) ? w->hi : nullptr,
                                                           (f32 && acc == FURAX_ACC_F32_KAHAN) ? w->lo : nullptr,
                                                           (acc == FURAX_ACC_F64) ? w->acc64 : nullptr, b.np_cg);
@@ -851,7 +855,7 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
             double mr = 0.0;
             for (int i = 0; i < p->n_obs; ++i)
                 mr = std::max(mr, w->h_sc[i].bb > 0 ? std::sqrt(w->h_sc[i].rr / w->h_sc[i].bb) : 0.0);
-            axpy_kernel<<<vgrid(3 * np), VT, 0, st>>>(x, w->e, 3 * np);
+            axpy_kernel<<<vgrid(p, 3 * np), VT, 0, st>>>(x, w->e, 3 * np);
             count_launches(1);
             if ((rc = check_launch("defect correction update"))) return rc;
             ++outer;

@@ -68,6 +68,10 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert lib.furax_gapfill(None, None, None, None, None, 0, 10, ctypes.c_double(1e-8), 1, None, None) == -1
     assert b"covariance" in lib.furax_last_error()
     assert lib.furax_templates_destroy(None) == 0
+    # bounded-wait controls
+    assert lib.furax_set_wait_budget(None, ctypes.c_int64(1 << 20), None) == -1
+    assert lib.furax_debug_hold_loader(None, 1, None) == -1
+    assert b"handle" in lib.furax_last_error()
 
 
 def test_python_binding_names_match_c_abi():

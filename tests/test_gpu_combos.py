@@ -7,15 +7,12 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 from oracle import templates as ot
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    a = a.cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
-    b = b.cpu().numpy() if torch.is_tensor(b) else np.asarray(b)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def demono(m, v):

@@ -6,14 +6,13 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(1, 1), (2, 3), (3, 5), (1, 63), (2, 64), (3, 65), (2, 127), (1, 4095), (2, 4097), (5, 6001)]
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 @pytest.fixture(scope="module")

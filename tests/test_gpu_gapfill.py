@@ -4,13 +4,12 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 from oracle import gapfill as og
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 # streams of 1 sample, shorter than the band, one tile, several tiles with a ragged tail

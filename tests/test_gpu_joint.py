@@ -5,12 +5,11 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 def obs_list(shapes, ids):

@@ -6,13 +6,12 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 from oracle import templates as ot
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 # streams of one sample, shorter than the band, one block, an odd and an even number of blocks

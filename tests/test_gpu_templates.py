@@ -5,13 +5,12 @@ import pytest
 import torch
 
 import synth
+from parity import rel
 from oracle import templates as ot
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 # ragged batch: streams shorter than the band, one tile, several tiles with a ragged tail
