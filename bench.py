@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--nside", type=int, default=None, help="override nside (profiling runs)")
     ap.add_argument("--acc", default=HEADLINE_ACC, choices=["f32", "f32_kahan", "f64"],
                     help="per-pixel accumulation of --apply-only runs")
+    ap.add_argument("--schedule", default=None, choices=["time_ordered", "pixel_sorted"],
+                    help="operator schedule of --apply-only runs (default: the bench's)")
+    ap.add_argument("--tile-len", type=int, default=0)
+    ap.add_argument("--max-rows", type=int, default=12)
+    ap.add_argument("--group-tol", type=float, default=2.0)
     global ARGS
     ARGS = ap.parse_args()
     return ARGS
@@ -811,6 +816,8 @@ def main():
     d_h = d.cpu().pin_memory()
 
     if args.apply_only:
+        if args.schedule:
+            P.set_schedule(args.schedule, tile_len=args.tile_len, max_rows=args.max_rows, group_tol=args.group_tol)
         xin = torch.randn(npix, 3, dtype=torch.float64, device=dev, generator=g)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
@@ -822,7 +829,7 @@ def main():
             stream.synchronize()
             nat.furax_profile_enable(False)
         ms, n = nat.furax_profile_read(0)
-        print(json.dumps({"apply_only": True, **wl, "acc": args.acc, "ms_per_apply": ms / max(n, 1),
+        print(json.dumps({"apply_only": True, **wl, "acc": args.acc, "schedule": P.schedule(), "ms_per_apply": ms / max(n, 1),
                           "gsamples_per_s": S / (ms / max(n, 1) / 1e3) / 1e9, "launches": n}), flush=True)
         return
 

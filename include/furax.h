@@ -82,6 +82,26 @@ typedef struct furax_pointing furax_pointing_t;
 typedef struct furax_noise furax_noise_t;
 typedef struct furax_templates furax_templates_t;
 
+/* How the cached FP32 normal operator walks the samples (furax_pointing_set_schedule). It changes
+ * the order of the floating-point additions only, never the operator or the accumulation mode.
+ *   FURAX_SCHED_TIME_ORDERED: tiles of one detector x 4096 consecutive samples; every sample does
+ *     one gather of its pixel and one reduction into it.
+ *   FURAX_SCHED_PIXEL_SORTED: tiles of the detectors whose tracks on the sky coincide (one column
+ *     of the focal plane along the scan: equal cross-scan offsets within group_tol pixel widths,
+ *     at most max_rows of them) over tile_len samples each; the samples of a tile, sorted by pixel
+ *     once per pointing refresh, gather each pixel once and accumulate each pixel's run of samples
+ *     with one reduction (the block decomposition P^T N^-1 P = sum_i P_i^T N_i^-1 P_i of
+ *     "Algebraic reductions", taken over such tiles). Templates keep the time-ordered kernel. */
+#define FURAX_SCHED_TIME_ORDERED 0
+#define FURAX_SCHED_PIXEL_SORTED 1
+typedef struct {
+    int32_t kernel;     /* FURAX_SCHED_TIME_ORDERED or FURAX_SCHED_PIXEL_SORTED */
+    int32_t tile_len;   /* pixel-sorted: samples per detector row, a multiple of 16 in [16, 4096]; 0 = as
+                           many as the tile's stage holds for its rows */
+    int32_t max_rows;   /* pixel-sorted: detectors per tile, 1..16 */
+    double group_tol;   /* pixel-sorted: cross-scan grouping tolerance in pixel widths (> 0) */
+} furax_schedule;
+
 /* A batch of observations: each with its own map, or sharing maps by map_id. */
 typedef struct {
     int32_t n_obs;            /* >= 1 */
@@ -126,6 +146,17 @@ furax_status furax_pointing_info(const furax_pointing_t *p, int64_t *nsamp_total
 /* Recompute the cached pixels and weights from the quaternion arrays given at creation (their
  * contents may have changed, their shapes may not). No-op for FURAX_POINTING_ON_THE_FLY. */
 furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream);
+
+/* Choose how the cached FP32 normal operator of this handle walks its samples (see
+ * furax_schedule). A pixel-sorted schedule builds its tiles from the detectors' focal-plane
+ * offsets and the direction of the boresight's motion (read from q_det and a few q_bore samples),
+ * allocates its permutation (about 3 bytes per sample, owned by the handle) and sorts it;
+ * furax_pointing_refresh re-sorts it. Synchronises `stream`. Errors: FURAX_EINVAL for a pointing
+ * without an FP32 cache (modes FURAX_POINTING_CACHE_F32 / _MIXED) or out-of-range fields,
+ * FURAX_ENOMEM. The default is FURAX_SCHED_TIME_ORDERED. */
+furax_status furax_pointing_set_schedule(furax_pointing_t *p, const furax_schedule *s, void *stream);
+/* The handle's current schedule. */
+furax_status furax_pointing_get_schedule(const furax_pointing_t *p, furax_schedule *s);
 
 /* Replace the per-detector polarisation-angle offsets (device [sum ndet] rad, or NULL for none).
  * Weights become (cos 2(psi+delta), sin 2(psi+delta)), or with a half-wave plate

@@ -45,6 +45,14 @@ class CgOpts(ctypes.Structure):
                 ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32), ("d_ready", ctypes.c_void_p)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("tile_len", ctypes.c_int32), ("max_rows", ctypes.c_int32),
+                ("group_tol", ctypes.c_double)]
+
+
+FURAX_SCHED_TIME_ORDERED, FURAX_SCHED_PIXEL_SORTED = 0, 1
+
+
 class CgResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("n_valid", ctypes.c_int64),
@@ -61,6 +69,8 @@ _SIGS = {
     "furax_pointing_cache": [_V, _V, _V, _V, _V],
     "furax_device_status": [_V, _V],
     "furax_set_wait_budget": [_V, _I64, _V],
+    "furax_pointing_set_schedule": [_V, ctypes.POINTER(Schedule), _V],
+    "furax_pointing_get_schedule": [_V, ctypes.POINTER(Schedule)],
     "furax_probe_convert": [_V, _V, _V, _V, _I64, _V],
     "furax_probe_fma": [_I32, _I64, _V, ctypes.POINTER(_D), _V],
     "furax_probe_l2": [_I32, _V, _I64, _V, _I64, _V, _V],
@@ -215,6 +225,18 @@ def furax_pointing_refresh(h, stream=None) -> None:
 def furax_device_status(h, stream=None) -> None:
     """Raise FuraxError (FURAX_ETIMEOUT) if a bounded device-side wait gave up."""
     _call("furax_device_status", h, _stream(stream))
+
+
+def furax_pointing_set_schedule(h, kernel: int, tile_len: int = 0, max_rows: int = 12, group_tol: float = 2.0,
+                                stream=None) -> None:
+    sch = Schedule(int(kernel), int(tile_len), int(max_rows), float(group_tol))
+    _call("furax_pointing_set_schedule", h, ctypes.byref(sch), _stream(stream))
+
+
+def furax_pointing_get_schedule(h) -> dict:
+    sch = Schedule()
+    _call("furax_pointing_get_schedule", h, ctypes.byref(sch))
+    return dict(kernel=sch.kernel, tile_len=sch.tile_len, max_rows=sch.max_rows, group_tol=sch.group_tol)
 
 
 def furax_set_wait_budget(h, cycles: int, stream=None) -> None:

@@ -276,13 +276,30 @@ furax_status furax_pointing_refresh(furax_pointing_t *p, void *stream)
         rc = launch_expand(p, p->pix, p->c32, p->s32, nullptr, nullptr, nullptr, st, false, p->c32lo, p->s32lo);
     else rc = launch_expand(p, p->pix, nullptr, nullptr, p->c64, p->s64, nullptr, st, false);
     p->has_psi = had;
+    if (!rc) rc = sort_sorted_tiles(p, st);   // the pixel-sorted tiles follow the new cache
     return rc;
+}
+
+furax_status furax_pointing_set_schedule(furax_pointing_t *p, const furax_schedule *s, void *stream)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    REQUIRE(s, "schedule is NULL");
+    return set_schedule(p, *s, (cudaStream_t)stream);
+}
+
+furax_status furax_pointing_get_schedule(const furax_pointing_t *p, furax_schedule *s)
+{
+    REQUIRE(p, "pointing handle is NULL");
+    REQUIRE(s, "schedule is NULL");
+    *s = p->sched;
+    return FURAX_OK;
 }
 
 static void pointing_free(furax_pointing *p)
 {
     if (!p) return;
     destroy_cg_ws(p);
+    free_sorted(p);
     cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs); cudaFree(p->d_hwp_cs);
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
     cudaFree(p->c32lo); cudaFree(p->s32lo); cudaFree(p->ws_bore_m);
@@ -505,6 +522,20 @@ __global__ void noise_prep_kernel(int kind, const double *__restrict__ in, int64
     }
 }
 
+// Band in tap order as duplicated pairs for the pixel-sorted operator: out[d][2j] = out[d][2j+1] =
+// c_|j-63| (zero past the band and for j = 127).
+__global__ void band_pairs_kernel(const float *__restrict__ p32, int32_t ntaps, int64_t ndet, float *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndet * kBandPairs) return;
+    const int64_t d = i / kBandPairs;
+    const int j = (int)(i % kBandPairs);
+    const int k = j < 63 ? 63 - j : j - 63;
+    const float c = (j < 127 && k < ntaps) ? p32[d * ntaps + k] : 0.f;
+    out[2 * i] = c;
+    out[2 * i + 1] = c;
+}
+
 furax_status furax_noise_create(int32_t kind, const double *params, int32_t ntaps, const furax_obs_desc *desc,
                                 void *stream, furax_noise_t **out)
 {
@@ -553,6 +584,18 @@ furax_status furax_noise_create(int32_t kind, const double *params, int32_t ntap
                                                                                     n->p32, n->diag, ndet);
     count_launches(1);
     if (!(rc = check_launch("noise create")) && long_band(n)) rc = prepare_noise_fft(n, L.obs, (cudaStream_t)stream);
+    if (!rc && kind == FURAX_NOISE_BANDED && !long_band(n)) {
+        if (cudaMalloc((void **)&n->band2, sizeof(float) * kBandPairs * 2 * (size_t)ndet) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(FURAX_ENOMEM, "noise band table allocation failed");
+        } else {
+            const int64_t nb = ndet * kBandPairs;
+            band_pairs_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n->p32, ntaps, ndet,
+                                                                                              n->band2);
+            count_launches(1);
+            rc = check_launch("noise band table");
+        }
+    }
     if (rc) {
         furax_noise_destroy(n);
         return rc;
@@ -565,7 +608,7 @@ furax_status furax_noise_destroy(furax_noise_t *n)
 {
     if (!n) return FURAX_OK;
     cudaDeviceSynchronize();
-    cudaFree(n->p64); cudaFree(n->p32); cudaFree(n->diag); cudaFree(n->d_obs); cudaFree(n->d_tiles);
+    cudaFree(n->p64); cudaFree(n->p32); cudaFree(n->diag); cudaFree(n->d_obs); cudaFree(n->d_tiles); cudaFree(n->band2);
     cudaFree(n->fft_items); cudaFree(n->tw64); cudaFree(n->tw32); cudaFree(n->spec64); cudaFree(n->spec32);
     cudaFree(n->gf_y); cudaFree(n->gf_r); cudaFree(n->gf_p); cudaFree(n->gf_q); cudaFree(n->gf_x32); cudaFree(n->gf_n32);
     cudaFree(n->gf_sc);

@@ -41,6 +41,17 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s)
     return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
+// Rounding error of each component of the FP32 addition old + v that an atomic performed.
+__device__ __forceinline__ float4 kahan_error_v4(float4 old, float4 v)
+{
+    float4 e;
+    e.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
+    e.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
+    e.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
+    e.w = 0.f;
+    return e;
+}
+
 // Compensated accumulation: the atomic returns the value it added to, so the exact
 // rounding error of that addition can be recomputed here and accumulated in `lo`.
 // hi + lo then equals the exact sum up to second-order terms, whatever the order in

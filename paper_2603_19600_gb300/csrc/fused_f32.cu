@@ -166,6 +166,9 @@ furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, con
     if (ft && !fused_f32_projects_templates(p))
         return set_error(FURAX_EINVAL, "template work is fused only for the cached FP32 pointing");
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
+    else if ((p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED) && !ft &&
+             sorted_active(p) && !long_band(n))
+        rc = launch_fused_sorted(p, n, x32, acc, hi, lo, a64, st);   // pixel-sorted schedule
     else if (p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED)  // FP32 weights: hi
         rc = launch_fused_tma(p, n, x32, acc, hi, lo, a64, st, ft);
     else rc = dispatch_fused_f32<2>(p, n, x32, acc, hi, lo, a64, st);
@@ -187,6 +190,7 @@ static furax_status prep_f32_mode_band()
 furax_status prepare_fused_f32()
 {
     furax_status rc = prepare_fused_tma();
+    if (!rc) rc = prepare_fused_sorted();
     if (!rc) rc = prep_f32_mode_band<0, true>();
     if (!rc) rc = prep_f32_mode_band<0, false>();
     if (!rc) rc = prep_f32_mode_band<1, true>();

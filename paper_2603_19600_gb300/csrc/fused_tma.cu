@@ -37,6 +37,8 @@ constexpr int kXsStages = 2;
 constexpr int kRawN = 4232;
 static_assert(kRawN % 4 == 0 && kRawN >= TILE + 2 * kHalo + 6, "raw stage must hold an aligned tile + halos");
 constexpr int kGatherPer = (TILE + 2 * kHalo + 32 * kTmaGather - 1) / (32 * kTmaGather);
+constexpr int kKahanBatch = 4;                     // returning atomics in flight per consumer thread
+static_assert(kConsOut % kKahanBatch == 0, "Kahan batches tile a thread's outputs");
 
 struct TmaSmem {
     int32_t pix[kRawStages][kRawN];
@@ -298,23 +300,51 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const int64_t shift = sp.row + tl.t0 - sp.g0;   // stage index of core sample u
         double2 cs = make_double2(1.0, 0.0);
         if (pv.psi_cs) cs = pv.psi_cs[gdet];
+        if constexpr (ACC == FURAX_ACC_F32_KAHAN) {
+            // The compensation needs each atomic's old value: issue kKahanBatch returning atomics
+            // back to back, then their error reductions, so that a thread has a batch in flight
+            // instead of one round trip per sample.
+#pragma unroll
+            for (int k0 = 0; k0 < kConsOut; k0 += kKahanBatch) {
+                float4 old[kKahanBatch];
+                float3 v[kKahanBatch];
+                int32_t px[kKahanBatch];
+#pragma unroll
+                for (int b = 0; b < kKahanBatch; ++b) {
+                    const int u = tid + (k0 + b) * 32 * kTmaConsumer;
+                    px[b] = u < tl.len ? S.pix[r][u + shift] : -1;
+                    if (px[b] >= 0) {
+                        float c = S.c[r][u + shift], s = S.s[r][u + shift];
+                        if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+                        const float yv = ys[spos(u)];
+                        v[b] = make_float3(yv, yv * c, yv * s);
+                        old[b] = atom_add_v4(acc_hi + ob.map_off + px[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f));
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < kKahanBatch; ++b)
+                    if (px[b] >= 0)
+                        red_add_v4(acc_lo + ob.map_off + px[b],
+                                   kahan_error_v4(old[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f)));
+            }
+        } else {
 #pragma unroll 4
-        for (int k = 0; k < kConsOut; ++k) {
-            const int u = tid + k * 32 * kTmaConsumer;
-            if (u >= tl.len) break;
-            const int32_t pix = S.pix[r][u + shift];
-            if (pix < 0) continue;
-            float c = S.c[r][u + shift], s = S.s[r][u + shift];
-            if (pv.psi_cs) rotate_psi<float>(c, s, cs);
-            const float yv = ys[spos(u)];
-            const int64_t gp = ob.map_off + pix;
-            const float4 v = make_float4(yv, yv * c, yv * s, 0.f);
-            if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
-            else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
-            else {
-                red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
-                red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
-                red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
+            for (int k = 0; k < kConsOut; ++k) {
+                const int u = tid + k * 32 * kTmaConsumer;
+                if (u >= tl.len) break;
+                const int32_t pix = S.pix[r][u + shift];
+                if (pix < 0) continue;
+                float c = S.c[r][u + shift], s = S.s[r][u + shift];
+                if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+                const float yv = ys[spos(u)];
+                const int64_t gp = ob.map_off + pix;
+                const float4 v = make_float4(yv, yv * c, yv * s, 0.f);
+                if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
+                else {
+                    red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
+                    red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
+                    red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
+                }
             }
         }
         mbar_arrive(&S.xs_empty[q]);

@@ -16,6 +16,7 @@ constexpr int PTILE = 4096;     // pixels per pixel tile (vector kernels, per-ob
 constexpr int MAXTAPS = 64;     // longest band of the fused kernels (c_0..c_63)
 constexpr int kLongTaps = 2048; // longest band of the overlap-save N^-1 (TOD in HBM)
 constexpr int kCtlWords = 4;    // device control block of a pointing handle (error, hold, wait budget)
+constexpr int kBandPairs = 128; // band of the fused kernels in tap order (127 taps + one zero), as FP32 pairs
 
 struct ObsInfo {
     int64_t nsamp;     // samples per detector
@@ -45,6 +46,24 @@ struct FftItem {       // two consecutive overlap-save blocks of one detector st
     int32_t det;       // local detector index within the observation
 };
 
+// A pixel-sorted tile (fused_sorted.cu): nrow detectors of one observation whose tracks on the sky
+// coincide (one column of the focal plane along the scan), over the core samples [t0, t0 + len)
+// of each, with the band's halos. Its gathered samples, sorted by pixel once per pointing refresh,
+// are perm[perm_off .. perm_off + perm_n[tile]) (entries: row << 12 | stage position in the row).
+struct STile {
+    int64_t t0;
+    int64_t perm_off;  // first uint16 entry (a multiple of 8: 16-byte aligned)
+    int32_t obs;
+    int32_t len;       // core samples per row
+    int32_t nrow;      // detectors (rows), <= kSRowMax
+    int32_t det0;      // first entry of the tile's rows in the sorted-detector list (local indices)
+};
+constexpr int kSNE = 4096;     // stage entries of a pixel-sorted tile (all rows, halos included)
+constexpr int kSRowMax = 16;   // rows per pixel-sorted tile (4 bits of a permutation entry)
+// Row stride of a pixel-sorted tile in stage entries: core + two band halos + up to 3 + 3 entries
+// of 16-byte alignment of the copied range, rounded to 4.
+__host__ __device__ constexpr int srow_stride(int len) { return (len + 2 * 63 + 6 + 3) & ~3; }
+
 struct PTile {         // pixels [p0, p0+len) of one observation (global map indices)
     int64_t p0;
     int32_t obs;
@@ -70,6 +89,7 @@ struct NoiseView {
     const double *p64;      // white: inverse variance [ndet]; banded: taps [ndet][ntaps]
     const float *p32;
     const double *diag;     // diagonal of N^-1 per detector [ndet] (FP64)
+    const float *band2;     // banded (<= MAXTAPS taps): [ndet][2 kBandPad] band in tap order as duplicated pairs
 };
 
 // Template work folded into the fused FP32 operator (see fused_tma.cu).
@@ -158,6 +178,14 @@ struct furax_pointing {
     int32_t *ws_hits = nullptr;       // [npix] hit counts when the caller passes none
     float *ws_bore_m = nullptr;       // [nbore][18] boresight rotation matrices (double-FP32)
     fx::CgWs *cg = nullptr;           // solver workspace (allocated by the first solve)
+    // operator schedule (furax_pointing_set_schedule); pixel-sorted tiles and their permutation
+    furax_schedule sched{};
+    fx::STile *d_stiles = nullptr;
+    int64_t n_stiles = 0;
+    int32_t *d_sdet = nullptr;        // detectors of the sorted tiles' rows, grouped (local indices)
+    uint16_t *d_perm = nullptr;       // per tile: gathered samples sorted by pixel
+    int32_t *d_perm_n = nullptr;      // per tile: entries of its permutation
+    int64_t perm_cap = 0;
     fx::PointingView view() const {
         return fx::PointingView{d_obs, q_bore, q_det, has_psi ? d_psi_cs : nullptr, pix, c32, s32, c32lo, s32lo, c64, s64,
                                 has_hwp ? d_hwp_cs : nullptr};
@@ -207,7 +235,8 @@ struct furax_noise {
     double *gf_y = nullptr, *gf_r = nullptr, *gf_p = nullptr, *gf_q = nullptr;
     float *gf_x32 = nullptr, *gf_n32 = nullptr;
     void *gf_sc = nullptr;
-    fx::NoiseView view() const { return fx::NoiseView{kind, ntaps, p64, p32, diag}; }
+    float *band2 = nullptr;     // banded, <= MAXTAPS taps: [ndet][256] band in tap order as duplicated pairs
+    fx::NoiseView view() const { return fx::NoiseView{kind, ntaps, p64, p32, diag, band2}; }
 };
 
 namespace fx {
@@ -260,6 +289,17 @@ furax_status prepare_kernels();
 furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, const void *d, int d_t,
                               const double *m, double *chi2, double *grad_map, double *grad_psi, int precision,
                               cudaStream_t st);
+
+// ---- pixel-sorted operator (fused_sorted.cu)
+// Build (or drop, for the time-ordered kernel) the pixel-sorted tiles of a cached FP32 pointing and
+// sort them; synchronises st. The permutation follows the cache: sort_sorted_tiles after a refresh.
+furax_status set_schedule(furax_pointing *p, const furax_schedule &s, cudaStream_t st);
+furax_status sort_sorted_tiles(const furax_pointing *p, cudaStream_t st);
+bool sorted_active(const furax_pointing *p);
+void free_sorted(furax_pointing *p);
+furax_status launch_fused_sorted(const furax_pointing *p, const furax_noise *n, const float4 *x32, int acc, float4 *hi,
+                                 float4 *lo, double *a64, cudaStream_t st);
+furax_status prepare_fused_sorted();
 
 // ---- launchers (fused.cu)
 // acc_* workspaces must be zeroed by the caller; x32 is the padded FP32 copy of the (masked) input.

@@ -61,7 +61,8 @@ __device__ __forceinline__ void fma_f32x2(unsigned long long &d, unsigned long l
 
 // R consecutive outputs per thread (R even): y[r] = sum_j c_|j-63| x[base + r + j] (x in skewed
 // slots), accumulated as pairs (y_i, y_{i+R/2}).
-template <int R>
+// GTAPS: T2 lives in global memory (read through the read-only cache) rather than shared memory.
+template <int R, bool GTAPS = false>
 __device__ __forceinline__ void band_product_x2(const float *__restrict__ xs, const float *__restrict__ T2, int base,
                                                 float (&y)[R])
 {
@@ -74,8 +75,16 @@ __device__ __forceinline__ void band_product_x2(const float *__restrict__ xs, co
     }
 #pragma unroll
     for (int j2 = 0; j2 < kBandPad; j2 += 2) {
-        const ulonglong2 cc = *reinterpret_cast<const ulonglong2 *>(T2 + 2 * j2);
-        const unsigned long long cpair[2] = {cc.x, cc.y};
+        unsigned long long cpair[2];
+        if constexpr (GTAPS) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(T2 + 2 * j2));
+            cpair[0] = pack_f32x2(f.x, f.y);
+            cpair[1] = pack_f32x2(f.z, f.w);
+        } else {
+            const ulonglong2 cc = *reinterpret_cast<const ulonglong2 *>(T2 + 2 * j2);
+            cpair[0] = cc.x;
+            cpair[1] = cc.y;
+        }
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
             const int j = j2 + jj;

@@ -85,6 +85,19 @@ class Pointing:
         except Exception:
             pass
 
+    def set_schedule(self, kernel="time_ordered", tile_len=0, max_rows=12, group_tol=2.0):
+        """How the cached FP32 normal operator walks the samples: "time_ordered" (one detector x
+        4096 samples per tile) or "pixel_sorted" (detectors on one track x tile_len samples, samples
+        sorted by pixel once per refresh; see furax_schedule). Only the order of the floating-point
+        additions changes."""
+        k = {"time_ordered": nat.FURAX_SCHED_TIME_ORDERED, "pixel_sorted": nat.FURAX_SCHED_PIXEL_SORTED}[kernel]
+        nat.furax_pointing_set_schedule(self.handle, k, tile_len, max_rows, group_tol)
+
+    def schedule(self) -> dict:
+        s = nat.furax_pointing_get_schedule(self.handle)
+        s["kernel"] = "pixel_sorted" if s["kernel"] == nat.FURAX_SCHED_PIXEL_SORTED else "time_ordered"
+        return s
+
     def refresh(self):
         """Recompute the cached pointing from the (possibly updated) quaternion tensors."""
         nat.furax_pointing_refresh(self.handle)

@@ -72,6 +72,8 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert lib.furax_set_wait_budget(None, ctypes.c_int64(1 << 20), None) == -1
     assert lib.furax_debug_hold_loader(None, 1, None) == -1
     assert b"handle" in lib.furax_last_error()
+    assert lib.furax_pointing_set_schedule(None, None, None) == -1
+    assert lib.furax_pointing_get_schedule(None, None) == -1
 
 
 def test_python_binding_names_match_c_abi():

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from parity import rel
+from parity import elem, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,7 @@ def test_largest_nside_pixels_bit_exact(fx, dev, orc, mode):
     assert np.max(np.abs(c.cpu().numpy()[ok] - oc.ravel()[ok])) < tol
 
 
-@pytest.mark.parametrize("mode,prec,tol", [("cache_f32", "f32", 2e-6), ("on_the_fly", "f64", 1e-12)])
+@pytest.mark.parametrize("mode,prec,tol", [("cache_f32", "f32", 137 * 2.0 ** -24), ("on_the_fly", "f64", 1e-13)])
 def test_tiny_and_odd_streams_with_hwp(fx, dev, orc, mode, prec, tol):
     """The same ragged shapes with a rotating half-wave plate on every observation."""
     obs = [synth.Observation(8, synth.satellite_scan(ns, t0=5.0 * i), synth.hex_focal_plane(nd),
@@ -93,6 +93,11 @@ def test_tiny_and_odd_streams_with_hwp(fx, dev, orc, mode, prec, tol):
     off = 0
     for o, xi in zip(obs, x):
         pix, c, s, _ = orc.pointing(o.nside, o.q_bore, o.q_det, hwp=o.hwp)
-        ref = orc.apply_ata(o.npix, pix, c, s, orc.Noise(taps=taps[:o.ndet]), None, xi)
-        assert rel(got[off:off + o.npix], ref) < tol, (o.ndet, o.nsamp)
+        on = orc.Noise(taps=taps[:o.ndet])
+        ref = orc.apply_ata(o.npix, pix, c, s, on, None, xi)
+        # per element against |P^T||N^-1||P||x|: in FP32 the weights (rounded once, 2^-24), the map
+        # and the 127-term band in FP32 arithmetic bound the error by ~(129 + 8) u
+        scale = orc.apply_ata(o.npix, pix, np.abs(c), np.abs(s), orc.Noise(taps=np.abs(taps[:o.ndet])), None,
+                              np.abs(xi))
+        assert elem(got[off:off + o.npix], ref, scale) < tol, (o.ndet, o.nsamp)
         off += o.npix

@@ -89,8 +89,10 @@ def test_joint_solve_matches_oracle(fx, dev, joint_case, precision, mode, tol):
     P = fx.Pointing.from_observations(obs, mode=mode, device=dev)
     assert P.npix_total == obs[0].npix
     N = fx.Noise.banded(P, taps)
+    # both sides solve to a relative residual of 1e-12, so that the stopping point does not decide the
+    # per-component comparison (Q and U are ~100 times smaller than I)
     x, valid, info = fx.mapmaker_cg(P, N, torch.as_tensor(d.ravel().astype(np.float32), device=dev), maxiter=400,
-                                    tol=1e-11, precision=precision)
+                                    tol=1e-12, precision=precision)
     assert info.converged
     v = valid.cpu().numpy()
     assert np.array_equal(v, bjd["valid"])
