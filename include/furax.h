@@ -158,6 +158,23 @@ furax_status furax_pointing_set_schedule(furax_pointing_t *p, const furax_schedu
 /* The handle's current schedule. */
 furax_status furax_pointing_get_schedule(const furax_pointing_t *p, furax_schedule *s);
 
+/* Autotuner of the schedule: for each of the ncand candidate schedules (host array), set it on
+ * the handle, run the fused FP32 normal operator once untimed and `reps` times timed (CUDA events
+ * on `stream` around each launch, a zero input map, accumulators cleared outside the timed
+ * interval) with the given accumulation (FURAX_ACC_*, never changed by the search), and write the
+ * mean milliseconds per launch to ms_out[k] (host, -1 for a candidate the handle rejects). The
+ * fastest is left set on the handle and its index written to *best_out. Synchronises `stream`
+ * repeatedly; allocates the handle's operator workspaces. Errors: FURAX_EINVAL for a pointing
+ * without an FP32 cache, a band longer than 64 taps, bad arguments or no valid candidate (the
+ * previous schedule is then restored); a device error ends the search the same way. The paper has
+ * no counterpart: its operators are compiled by XLA. */
+furax_status furax_autotune(furax_pointing_t *p, const furax_noise_t *n, int32_t acc, const furax_schedule *cand,
+                            int32_t ncand, int32_t reps, double *ms_out, int32_t *best_out, void *stream);
+/* The built-in search space: copies up to cap candidates into out (may be NULL) and returns how
+ * many there are: the time-ordered kernel, then the pixel-sorted kernel over tile_len
+ * {0, 128, 256, 512} x max_rows {4, 8, 12, 16} x group_tol {1, 2, 4}. */
+int32_t furax_autotune_space(furax_schedule *out, int32_t cap);
+
 /* Replace the per-detector polarisation-angle offsets (device [sum ndet] rad, or NULL for none).
  * Weights become (cos 2(psi+delta), sin 2(psi+delta)), or with a half-wave plate
  * (cos(4w - 2(psi+delta)), sin(4w - 2(psi+delta))) - the offset rotation passes through the plate
@@ -267,6 +284,18 @@ furax_status furax_rhs(const furax_pointing_t *p, const furax_noise_t *n, const 
  * Table 1; maximum-likelihood and binned estimators, "Map-making classes").
  * ------------------------------------------------------------------------------------- */
 
+/* Sum over processes, for a map shared by processes that each hold a subset of its detectors
+ * (detector sharding of P^T N^-1 P = sum_i P_i^T N_i^-1 P_i, "Algebraic reductions"). The solver
+ * calls it with a device buffer of n elements (dtype FURAX_REDUCE_F64 or FURAX_REDUCE_I32) after
+ * enqueueing the work that produced it on `stream`; on return, or for every operation enqueued
+ * later on `stream`, buf must hold the elementwise sum over all processes (e.g. a collective
+ * enqueued on the stream, or a synchronisation, a host-side sum and a copy back). Every process
+ * must make the same sequence of calls with the same pointing layout (observations, nside, map
+ * ids). A non-zero return ends the solve with that status. */
+#define FURAX_REDUCE_F64 0
+#define FURAX_REDUCE_I32 1
+typedef furax_status (*furax_allreduce_fn)(void *buf, int64_t n, int32_t dtype, void *stream, void *user);
+
 typedef struct {
     int32_t maxiter;       /* cap on PCG iterations per observation (all outer steps together) */
     double tol;            /* stop when ||b - A x||/||b|| <= tol */
@@ -286,6 +315,13 @@ typedef struct {
     void *d_ready;         /* cudaEvent_t recorded once d is written (e.g. after its host-to-device
                               copy on another stream), or NULL: the solver waits for it only before
                               it reads d, so the copy overlaps the preconditioner set-up */
+    furax_allreduce_fn allreduce; /* NULL, or the detector-sharding sum: called on the
+                              preconditioner blocks and hit counts before their inversion, the
+                              right-hand side, every application of the normal operator (summed in
+                              FP64) and the true residual's operator; all vectors, dot products
+                              and scalars are then the same on every process. Disables graph
+                              capture; not available with templates */
+    void *allreduce_user;  /* passed to allreduce */
 } furax_cg_opts;
 
 typedef struct {

@@ -42,7 +42,35 @@ class CgOpts(ctypes.Structure):
     _fields_ = [("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("acc", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_every", ctypes.c_int32), ("rcond_min", ctypes.c_double),
-                ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32), ("d_ready", ctypes.c_void_p)]
+                ("binned_only", ctypes.c_int32), ("true_residual", ctypes.c_int32), ("d_ready", ctypes.c_void_p),
+                ("allreduce", ctypes.c_void_p), ("allreduce_user", ctypes.c_void_p)]
+
+
+FURAX_REDUCE_F64, FURAX_REDUCE_I32 = 0, 1
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_void_p)
+
+
+class _DeviceView:
+    """A device buffer of the library exposed through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, n: int, dtype: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8" if dtype == FURAX_REDUCE_F64 else "<i4",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def allreduce_callback(fn):
+    """Wrap fn(tensor) -> None, which sums a CUDA tensor in place over the processes of a sharded map
+    (on the current stream), as a furax_allreduce_fn. Keep the returned object alive during the solve."""
+
+    def cb(buf, n, dtype, stream, user):
+        try:
+            fn(torch.as_tensor(_DeviceView(buf, n, dtype), device=torch.device("cuda", torch.cuda.current_device())))
+            return 0
+        except Exception:  # noqa: BLE001 - reported to the solver as a status, which raises
+            return -3
+
+    return ALLREDUCE_FN(cb)
 
 
 class Schedule(ctypes.Structure):
@@ -71,6 +99,9 @@ _SIGS = {
     "furax_set_wait_budget": [_V, _I64, _V],
     "furax_pointing_set_schedule": [_V, ctypes.POINTER(Schedule), _V],
     "furax_pointing_get_schedule": [_V, ctypes.POINTER(Schedule)],
+    "furax_autotune": [_V, _V, _I32, ctypes.POINTER(Schedule), _I32, _I32, ctypes.POINTER(_D),
+                       ctypes.POINTER(_I32), _V],
+    "furax_autotune_space": [ctypes.POINTER(Schedule), _I32],
     "furax_probe_convert": [_V, _V, _V, _V, _I64, _V],
     "furax_probe_fma": [_I32, _I64, _V, ctypes.POINTER(_D), _V],
     "furax_probe_l2": [_I32, _V, _I64, _V, _I64, _V, _V],
@@ -237,6 +268,24 @@ def furax_pointing_get_schedule(h) -> dict:
     sch = Schedule()
     _call("furax_pointing_get_schedule", h, ctypes.byref(sch))
     return dict(kernel=sch.kernel, tile_len=sch.tile_len, max_rows=sch.max_rows, group_tol=sch.group_tol)
+
+
+def furax_autotune_space() -> list:
+    n = lib().furax_autotune_space(None, 0)
+    arr = (Schedule * n)()
+    lib().furax_autotune_space(arr, n)
+    return [dict(kernel=c.kernel, tile_len=c.tile_len, max_rows=c.max_rows, group_tol=c.group_tol) for c in arr]
+
+
+def furax_autotune(hp, hn, acc: int, candidates: list, reps: int = 3, stream=None):
+    """Time each candidate schedule (dicts of furax_schedule fields); returns (ms per candidate, best index)."""
+    n = len(candidates)
+    arr = (Schedule * n)(*[Schedule(int(c["kernel"]), int(c["tile_len"]), int(c["max_rows"]), float(c["group_tol"]))
+                           for c in candidates])
+    ms = (ctypes.c_double * n)()
+    best = _I32()
+    _call("furax_autotune", hp, hn, int(acc), arr, n, int(reps), ms, ctypes.byref(best), _stream(stream))
+    return [ms[i] for i in range(n)], best.value
 
 
 def furax_set_wait_budget(h, cycles: int, stream=None) -> None:

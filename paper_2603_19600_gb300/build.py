@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libfurax.so")
-SOURCES = ["abi.cu", "pointing.cu", "fused_f32.cu", "fused_f64.cu", "noise.cu", "solver.cu", "noalloc.cu", "fused_df.cu", "pointing_fast.cu", "fused_tma.cu", "templates.cu", "noise_fft.cu", "gapfill.cu", "probe.cu", "fused_sorted.cu"]
+SOURCES = ["abi.cu", "pointing.cu", "fused_f32.cu", "fused_f64.cu", "noise.cu", "solver.cu", "noalloc.cu", "fused_df.cu", "pointing_fast.cu", "fused_tma.cu", "templates.cu", "noise_fft.cu", "gapfill.cu", "probe.cu", "fused_sorted.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -36,6 +36,16 @@ furax_status check_cuda(cudaError_t e, const char *what)
 
 furax_status check_launch(const char *what) { return check_cuda(cudaGetLastError(), what); }
 
+furax_status AllReduce::operator()(void *buf, int64_t n, int32_t dtype, cudaStream_t st) const
+{
+    if (!fn || n <= 0) return FURAX_OK;
+    furax_status rc = check_launch("before the sharding sum");
+    if (rc) return rc;
+    rc = fn(buf, n, dtype, (void *)st, user);
+    if (rc) return set_error(rc < 0 ? rc : FURAX_EINVAL, "the sharding sum (allreduce) returned %d", rc);
+    return FURAX_OK;
+}
+
 void count_launches(int64_t n) { g_launches += n; }
 
 furax_status allow_smem(const void *kern, size_t bytes)
@@ -303,7 +313,7 @@ static void pointing_free(furax_pointing *p)
     cudaFree(p->d_obs); cudaFree(p->d_tiles); cudaFree(p->d_ptiles); cudaFree(p->d_psi_cs); cudaFree(p->d_hwp_cs);
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
     cudaFree(p->c32lo); cudaFree(p->s32lo); cudaFree(p->ws_bore_m);
-    cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc_lo); cudaFree(p->ws_acc64); cudaFree(p->ws_df_lo); cudaFree(p->ws_x64);
+    cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc64); cudaFree(p->ws_df_lo); cudaFree(p->ws_x64);
     cudaFree(p->ws_tod); cudaFree(p->ws_tod2); cudaFree(p->ws_hits); cudaFree(p->d_err);
     delete p;
 }
@@ -697,6 +707,8 @@ void furax_cg_default_opts(furax_cg_opts *o)
     o->binned_only = 0;
     o->true_residual = 1;
     o->d_ready = nullptr;
+    o->allreduce = nullptr;
+    o->allreduce_user = nullptr;
 }
 
 furax_status furax_mapmaker_cg(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t, double *x,
@@ -796,6 +808,7 @@ furax_status furax_mapmaker_cg_deproject(const furax_templates_t *t, const void 
             "mixed precision needs 0 <= inner_tol < 1 and max_outer >= 1");
     REQUIRE(o->check_every >= 1, "check_every must be >= 1");
     REQUIRE(!res->hist || res->hist_len >= 0, "hist_len must be >= 0");
+    REQUIRE(!o->allreduce, "detector sharding (allreduce) is not available with templates");
     return mapmaker_cg(t->p, t->n, d, d_t, x, valid, o, res, (cudaStream_t)stream, t, amplitudes);
 }
 

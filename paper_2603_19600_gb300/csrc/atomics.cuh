@@ -52,6 +52,12 @@ __device__ __forceinline__ float4 kahan_error_v4(float4 old, float4 v)
     return e;
 }
 
+// Compensated FP32 accumulators are interleaved: pixel i's sum is hi[2i] and its compensation
+// lo[2i], with lo = hi + 1, so both words of a pixel share one 32-byte sector and the reduction of
+// the rounding error hits the sector that the returning atomic just brought into L2. Plain FP32
+// accumulators are hi[i].
+constexpr int kKahanStride = 2;
+
 // Compensated accumulation: the atomic returns the value it added to, so the exact
 // rounding error of that addition can be recomputed here and accumulated in `lo`.
 // hi + lo then equals the exact sum up to second-order terms, whatever the order in

@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict
         const int64_t gp = ob.map_off + pix;
         const float4 v = make_float4(y[r], y[r] * c, y[r] * s, 0.f);
         if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
-        else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
+        else if constexpr (ACC == FURAX_ACC_F32_KAHAN)
+            kahan_add_v4(acc_hi + kKahanStride * gp, acc_lo + kKahanStride * gp, v);
         else {
             red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
             red_add_f64(acc64 + 3 * gp + 1, (double)v.y);

@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
                     int32_t pj;
                     if (j < np && run_head(j, pj) && run_sum(j, pj, hh[b], ll[b])) {
                         px[b] = pj;
-                        old[b] = atom_add_v4(acc_hi + ob.map_off + pj, make_float4(hh[b].x, hh[b].y, hh[b].z, 0.f));
+                        old[b] = atom_add_v4(acc_hi + kKahanStride * (ob.map_off + pj),
+                                             make_float4(hh[b].x, hh[b].y, hh[b].z, 0.f));
                     }
                 }
 #pragma unroll
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
                     if (px[b] >= 0) {
                         float4 e = kahan_error_v4(old[b], make_float4(hh[b].x, hh[b].y, hh[b].z, 0.f));
                         e.x += ll[b].x; e.y += ll[b].y; e.z += ll[b].z;
-                        red_add_v4(acc_lo + ob.map_off + px[b], e);
+                        red_add_v4(acc_lo + kKahanStride * (ob.map_off + px[b]), e);
                     }
             }
         } else {

@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     const float4 v = make_float4(a[0], tpl.order >= 1 ? a[1] : 0.f, tpl.order >= 2 ? a[2] : 0.f, 0.f);
                     const int64_t gp = tpl.base + gdet;
                     if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
-                    else if constexpr (ACC == FURAX_ACC_F32_KAHAN) kahan_add_v4(acc_hi + gp, acc_lo + gp, v);
+                    else if constexpr (ACC == FURAX_ACC_F32_KAHAN)
+                        kahan_add_v4(acc_hi + kKahanStride * gp, acc_lo + kKahanStride * gp, v);
                     else {
                         red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
                         red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
@@ -318,13 +319,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                         if (pv.psi_cs) rotate_psi<float>(c, s, cs);
                         const float yv = ys[spos(u)];
                         v[b] = make_float3(yv, yv * c, yv * s);
-                        old[b] = atom_add_v4(acc_hi + ob.map_off + px[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f));
+                        old[b] = atom_add_v4(acc_hi + kKahanStride * (ob.map_off + px[b]),
+                                             make_float4(v[b].x, v[b].y, v[b].z, 0.f));
                     }
                 }
 #pragma unroll
                 for (int b = 0; b < kKahanBatch; ++b)
                     if (px[b] >= 0)
-                        red_add_v4(acc_lo + ob.map_off + px[b],
+                        red_add_v4(acc_lo + kKahanStride * (ob.map_off + px[b]),
                                    kahan_error_v4(old[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f)));
             }
         } else {

@@ -109,6 +109,14 @@ struct TplView {
     const double *b;        // [ndet][4] template amplitudes of the last solve
 };
 
+// The caller's detector-sharding sum (furax_cg_opts.allreduce), or nothing.
+struct AllReduce {
+    furax_allreduce_fn fn = nullptr;
+    void *user = nullptr;
+    bool on() const { return fn != nullptr; }
+    furax_status operator()(void *buf, int64_t n, int32_t dtype, cudaStream_t st) const;
+};
+
 // Status helpers (thread-local message).
 furax_status set_error(furax_status code, const char *fmt, ...);
 furax_status check_cuda(cudaError_t e, const char *what);
@@ -168,8 +176,8 @@ struct furax_pointing {
                                       // loader hold flag, wait budget (mbarrier.cuh)
     // workspaces, allocated on first use and freed by destroy
     float4 *ws_map32 = nullptr;       // [npix] padded FP32 copy of a map for the gather
-    float4 *ws_acc_hi = nullptr;      // [npix] FP32 accumulator (I,Q,U,-)
-    float4 *ws_acc_lo = nullptr;      // [npix] FP32 compensation (KAHAN)
+    float4 *ws_acc_hi = nullptr;      // [2 npix] FP32 accumulator (I,Q,U,-): plain hi[i], or compensated
+                                      // hi[2i] with its compensation at hi[2i + 1] (atomics.cuh)
     double *ws_acc64 = nullptr;       // [npix][3] FP64 accumulator
     float4 *ws_df_lo = nullptr;       // [npix] FP32 low-word accumulator of the double-FP32 RHS
     double *ws_x64 = nullptr;         // [npix][3] masked FP64 copy
@@ -255,7 +263,7 @@ furax_status launch_P(const furax_pointing *p, const void *map, int map_t, void 
 furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void *map, int map_t, int acc,
                        int32_t *hits, int accumulate, cudaStream_t st);
 furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rcond_min, double *blocks_inv,
-                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st);
+                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st, const AllReduce &ar = AllReduce{});
 
 // ---- launchers (noise.cu)
 furax_status launch_ninv(const furax_noise *n, const void *in, void *out, int dtype, cudaStream_t st);

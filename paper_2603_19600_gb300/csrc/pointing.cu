@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(256) PT_kernel(const Tile *__restrict__ tiles,
         } else if constexpr (ACC == FURAX_ACC_F32) {
             red_add_v4(hi + gp, make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
         } else {
-            kahan_add_v4(hi + gp, lo + gp, make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
+            kahan_add_v4(hi + kKahanStride * gp, lo + kKahanStride * gp,
+                         make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
         }
         if (hits) red_add_s32(hits + gp, 1);
     }
@@ -197,9 +198,10 @@ __global__ void PT_finalize_kernel(int acc, const float4 *__restrict__ hi, const
         double v0, v1, v2;
         if (acc == FURAX_ACC_F64) { v0 = acc64[3 * p]; v1 = acc64[3 * p + 1]; v2 = acc64[3 * p + 2]; }
         else {
-            float4 h = hi[p];
+            const bool k = acc == FURAX_ACC_F32_KAHAN;
+            float4 h = hi[k ? kKahanStride * p : p];
             v0 = h.x; v1 = h.y; v2 = h.z;
-            if (acc == FURAX_ACC_F32_KAHAN) { float4 l = lo[p]; v0 += l.x; v1 += l.y; v2 += l.z; }
+            if (k) { float4 l = lo[kKahanStride * p]; v0 += l.x; v1 += l.y; v2 += l.z; }
         }
         if (accumulate) { v0 += (double)map[3 * p]; v1 += (double)map[3 * p + 1]; v2 += (double)map[3 * p + 2]; }
         map[3 * p] = (MT)v0; map[3 * p + 1] = (MT)v1; map[3 * p + 2] = (MT)v2;
@@ -253,14 +255,12 @@ furax_status launch_PT(const furax_pointing *p, const void *tod, int tod_t, void
         a64 = pm->ws_acc64;
         if ((rc = check_cuda(cudaMemsetAsync(a64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
     } else {
-        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_hi, sizeof(float4) * np))) return rc;
+        // room for the interleaved compensated layout (hi[2i], lo[2i] = hi[2i + 1])
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_hi, sizeof(float4) * kKahanStride * np))) return rc;
         hi = pm->ws_acc_hi;
-        if ((rc = check_cuda(cudaMemsetAsync(hi, 0, sizeof(float4) * np, st), "memset"))) return rc;
-        if (acc == FURAX_ACC_F32_KAHAN) {
-            if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_lo, sizeof(float4) * np))) return rc;
-            lo = pm->ws_acc_lo;
-            if ((rc = check_cuda(cudaMemsetAsync(lo, 0, sizeof(float4) * np, st), "memset"))) return rc;
-        }
+        if (acc == FURAX_ACC_F32_KAHAN) lo = hi + 1;
+        const size_t words = (acc == FURAX_ACC_F32_KAHAN ? kKahanStride : 1) * (size_t)np;
+        if ((rc = check_cuda(cudaMemsetAsync(hi, 0, sizeof(float4) * words, st), "memset"))) return rc;
     }
     if (hits && !accumulate)
         if ((rc = check_cuda(cudaMemsetAsync(hits, 0, sizeof(int32_t) * np, st), "memset"))) return rc;
@@ -369,7 +369,7 @@ __global__ void bj_invert_kernel(double *__restrict__ m6, const int32_t *__restr
 }
 
 furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rcond_min, double *blocks_inv,
-                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st)
+                       uint8_t *valid, int32_t *hits, double *rcond, cudaStream_t st, const AllReduce &ar)
 {
     furax_pointing *pm = const_cast<furax_pointing *>(p);
     const int64_t np = p->npix_total;
@@ -395,6 +395,9 @@ furax_status launch_bj(const furax_pointing *p, const furax_noise *n, double rco
         count_launches(1);
         if ((rc = check_launch("preconditioner accumulation"))) return rc;
     }
+    // detector sharding: the blocks and hits of every process's detectors, before the inversion
+    if (ar.on() && ((rc = ar(blocks_inv, 6 * np, FURAX_REDUCE_F64, st)) || (rc = ar(h, np, FURAX_REDUCE_I32, st))))
+        return rc;
     const unsigned fg = (unsigned)std::min<int64_t>((np + 255) / 256, 16LL * p->n_sm);
     bj_invert_kernel<<<fg, 256, 0, st>>>(blocks_inv, h, valid, rcond, np, rcond_min);
     count_launches(1);

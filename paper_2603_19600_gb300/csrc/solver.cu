@@ -68,7 +68,7 @@ static void free_cg(CgWs *w)
 {
     if (!w) return;
     cudaFree(w->r); cudaFree(w->z); cudaFree(w->p); cudaFree(w->q); cudaFree(w->minv); cudaFree(w->valid);
-    cudaFree(w->bfull); cudaFree(w->e); cudaFree(w->acc64); cudaFree(w->p32); cudaFree(w->hi); cudaFree(w->lo);
+    cudaFree(w->bfull); cudaFree(w->e); cudaFree(w->acc64); cudaFree(w->p32); cudaFree(w->hi);   // lo = hi + 1
     cudaFree(w->partial); cudaFree(w->sc); cudaFree(w->hist);
     for (cudaEvent_t e : w->ev) cudaEventDestroy(e);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -87,6 +87,14 @@ void destroy_cg_ws(furax_pointing *p)
 // Elementwise helpers
 // ------------------------------------------------------------------------------------
 
+// Clear pixel i of the FP32 accumulators: plain (za[i]) or compensated (zb = za + 1: za[2i], zb[2i]).
+__device__ __forceinline__ void zero_acc(float4 *za, float4 *zb, int64_t i)
+{
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zb) { za[kKahanStride * i] = z; zb[kKahanStride * i] = z; }
+    else if (za) za[i] = z;
+}
+
 // x32[p] = (float)x[p] on valid pixels (0 elsewhere); zero the FP32 accumulators.
 __global__ void pack_x32_kernel(const double *__restrict__ x, const uint8_t *__restrict__ valid, float4 *__restrict__ x32,
                                 float4 *__restrict__ za, float4 *__restrict__ zb, int64_t np)
@@ -94,8 +102,7 @@ __global__ void pack_x32_kernel(const double *__restrict__ x, const uint8_t *__r
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         const bool ok = !valid || valid[i];
         x32[i] = ok ? make_float4((float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (za) za[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (zb) zb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        zero_acc(za, zb, i);
     }
 }
 
@@ -103,9 +110,10 @@ __device__ __forceinline__ void acc_value(int acc, const float4 *hi, const float
                                           double &v0, double &v1, double &v2)
 {
     if (acc == FURAX_ACC_F64) { v0 = a64[3 * i]; v1 = a64[3 * i + 1]; v2 = a64[3 * i + 2]; return; }
-    const float4 h = hi[i];
+    const bool k = acc == FURAX_ACC_F32_KAHAN;   // interleaved: hi[2i], lo[2i] (atomics.cuh)
+    const float4 h = hi[k ? kKahanStride * i : i];
     v0 = h.x; v1 = h.y; v2 = h.z;
-    if (acc == FURAX_ACC_F32_KAHAN) { const float4 l = lo[i]; v0 += l.x; v1 += l.y; v2 += l.z; }
+    if (k) { const float4 l = lo[kKahanStride * i]; v0 += l.x; v1 += l.y; v2 += l.z; }
 }
 
 __global__ void finalize_acc_kernel(int acc, const float4 *__restrict__ hi, const float4 *__restrict__ lo,
@@ -249,12 +257,9 @@ furax_status ptnp_apply(const furax_pointing *p, const furax_noise *n, const dou
         a64 = pm->ws_acc64;
         if ((rc = check_cuda(cudaMemsetAsync(a64, 0, sizeof(double) * 3 * np, st), "memset"))) return rc;
     } else {
-        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_hi, sizeof(float4) * np))) return rc;
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_hi, sizeof(float4) * kKahanStride * np))) return rc;
         hi = pm->ws_acc_hi;
-        if (acc == FURAX_ACC_F32_KAHAN) {
-            if ((rc = ensure_ws(pm, (void **)&pm->ws_acc_lo, sizeof(float4) * np))) return rc;
-            lo = pm->ws_acc_lo;
-        }
+        if (acc == FURAX_ACC_F32_KAHAN) lo = hi + 1;   // interleaved compensated layout
     }
     if ((rc = launch_pack_x32(p, x, valid, pm->ws_map32, hi, lo, st))) return rc;
     double *tpl_a = tpl_fused_target(tp, p);
@@ -357,8 +362,7 @@ __global__ void cg_pack_kernel(const double *__restrict__ p, float4 *__restrict_
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         if (p32) p32[i] = make_float4((float)p[3 * i], (float)p[3 * i + 1], (float)p[3 * i + 2], 0.f);
-        if (za) za[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (zb) zb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        zero_acc(za, zb, i);
         if (z64) { z64[3 * i] = 0.0; z64[3 * i + 1] = 0.0; z64[3 * i + 2] = 0.0; }
     }
 }
@@ -458,8 +462,7 @@ __global__ void cg_dir_kernel(const PTile *__restrict__ pt, const CgScalars *__r
             p[3 * i + c] = pp[c];
         }
         if (p32) p32[i] = make_float4((float)pp[0], (float)pp[1], (float)pp[2], 0.f);
-        if (za) za[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (zb) zb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        zero_acc(za, zb, i);
         if (z64) { z64[3 * i] = 0.0; z64[3 * i + 1] = 0.0; z64[3 * i + 2] = 0.0; }
     }
 }
@@ -533,8 +536,9 @@ static furax_status get_ws(furax_pointing *p, int hist_cap, CgWs **out)
     if (!rc) rc = alloc((void **)&w->minv, sizeof(double) * 6 * (size_t)np);
     if (!rc) rc = alloc((void **)&w->valid, (size_t)np);
     if (!rc) rc = alloc((void **)&w->p32, sizeof(float4) * (size_t)np);
-    if (!rc) rc = alloc((void **)&w->hi, sizeof(float4) * (size_t)np);
-    if (!rc) rc = alloc((void **)&w->lo, sizeof(float4) * (size_t)np);
+    // FP32 accumulators: plain hi[i], or compensated interleaved hi[2i], lo[2i] with lo = hi + 1
+    if (!rc) rc = alloc((void **)&w->hi, sizeof(float4) * kKahanStride * (size_t)np);
+    if (!rc) w->lo = w->hi + 1;
     const int64_t nparts = p->n_ptiles + p->n_obs + p->ndet_total / PTILE + 1;   // also the augmented tiles
     if (!rc) rc = alloc((void **)&w->partial, sizeof(double) * KD * (size_t)nparts);
     if (!rc) rc = alloc((void **)&w->sc, sizeof(CgScalars) * p->n_obs);
@@ -566,6 +570,7 @@ struct Body {
     const ObsInfo *cobs;
     int64_t np_cg;
     bool aug;
+    AllReduce ar;                // detector sharding: sum of the operator's output over processes
 };
 
 // One PCG iteration: q = A p, alpha, x/r/z update, beta, new direction (+ accumulator reset).
@@ -593,6 +598,14 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
             return rc;
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    if (b.ar.on()) {
+        // detector sharding: this process's partial P^T N^-1 P p, in FP64, summed over processes
+        if (acc != FURAX_ACC_F64) {
+            if ((rc = launch_finalize_acc(p, acc, w->hi, w->lo, nullptr, nullptr, w->acc64, st))) return rc;
+            acc = FURAX_ACC_F64;
+        }
+        if ((rc = b.ar(w->acc64, 3 * p->npix_total, FURAX_REDUCE_F64, st))) return rc;
+    }
     if (b.tp && !b.aug) {
         const bool f64 = b.precision == FURAX_F64 || lb;
         if ((rc = launch_tpl_map(b.tp, f64 ? FURAX_F64 : FURAX_F32, acc, w->p32, w->p, w->hi, w->lo, w->acc64, st,
@@ -648,8 +661,9 @@ static furax_status pcg(const Body &b, const double *rhs, int maxiter, int use_g
     if ((rc = check_launch("PCG init"))) return rc;
     if ((rc = body_prologue(b, st))) return rc;
     check_every = std::max(1, check_every);
-    // Stream capture is not possible on the legacy default stream.
-    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) use_graph = 0;
+    // Stream capture is not possible on the legacy default stream, nor around the caller's
+    // sharding sum (host code).
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread || b.ar.on()) use_graph = 0;
     int done_iters = 0;
     *all_done = false;
     while (done_iters < maxiter) {
@@ -743,6 +757,7 @@ static furax_status true_residual(const Body &b, const double *x, double *rtrue,
     }
     if (b.tp && (rc = launch_tpl_map(b.tp, FURAX_F64, FURAX_ACC_F64, nullptr, x, nullptr, nullptr, w->acc64, st)))
         return rc;
+    if (b.ar.on() && (rc = b.ar(w->acc64, 3 * p->npix_total, FURAX_REDUCE_F64, st))) return rc;
     residual_kernel<<<b.pg, VT, 0, st>>>(p->d_ptiles, w->bfull, w->acc64, w->valid, rtrue, w->partial);
     double *norms = w->q;   // scratch [n_obs][2] (q is free here)
     obs_norms_kernel<<<p->n_obs, VT, 0, st>>>(p->d_obs, w->partial, norms);
@@ -770,8 +785,11 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
     const int64_t np = p->npix_total;
     const unsigned pg = (unsigned)std::max<int64_t>(1, p->n_ptiles);
 
-    // Preconditioner and mask (FP64 blocks from the handle's pointing).
-    if ((rc = launch_bj(p, n, o->rcond_min, w->minv, w->valid, nullptr, nullptr, st))) return rc;
+    const AllReduce ar{o->allreduce, o->allreduce_user};
+    if (ar.on() && tp) return set_error(FURAX_EINVAL, "detector sharding (allreduce) is not available with templates");
+    // Preconditioner and mask (FP64 blocks from the handle's pointing; summed over the processes
+    // of a sharded map before the inversion).
+    if ((rc = launch_bj(p, n, o->rcond_min, w->minv, w->valid, nullptr, nullptr, st, ar))) return rc;
     // Right-hand side b = S P^T N^-1 d in FP64 (the first read of d).
     if (o->d_ready && (rc = check_cuda(cudaStreamWaitEvent(st, (cudaEvent_t)o->d_ready, 0), "wait for d")))
         return rc;
@@ -791,13 +809,14 @@ furax_status mapmaker_cg(const furax_pointing *p, const furax_noise *n, const vo
             return rc;
     }
     if (tp && !tpl_folded && (rc = launch_tpl_rhs(tp, d, d_t, w->acc64, st))) return rc;
+    if (ar.on() && (rc = ar(w->acc64, 3 * np, FURAX_REDUCE_F64, st))) return rc;
     if ((rc = launch_finalize_acc(p, FURAX_ACC_F64, nullptr, nullptr, w->acc64, w->valid, w->bfull, st))) return rc;
     if (valid_out && (rc = check_cuda(cudaMemcpyAsync(valid_out, w->valid, np, cudaMemcpyDeviceToDevice, st), "copy mask")))
         return rc;
 
     // a long band accumulates in FP64 (its operator goes through the TOD in HBM)
     Body b{p, n, w, o->precision, long_band(n) ? FURAX_ACC_F64 : o->acc, o->tol * o->tol, x, pg, tp,
-           p->d_ptiles, p->d_obs, np, false};
+           p->d_ptiles, p->d_obs, np, false, ar};
     int total_iters = 0, outer = 0;
     bool converged = false;
     double rel = 0.0, true_rel = 0.0;

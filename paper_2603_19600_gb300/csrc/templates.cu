@@ -397,7 +397,8 @@ __global__ void __launch_bounds__(FT) tpl_scatter_kernel(const Tile *__restrict_
         if constexpr (ACC == FURAX_ACC_F32) {
             red_add_v4(hi + gp, make_float4(float(v), float(v * c), float(v * s), 0.f));
         } else if constexpr (ACC == FURAX_ACC_F32_KAHAN) {
-            kahan_add_v4(hi + gp, lo + gp, make_float4(float(v), float(v * c), float(v * s), 0.f));
+            kahan_add_v4(hi + kKahanStride * gp, lo + kKahanStride * gp,
+                         make_float4(float(v), float(v * c), float(v * s), 0.f));
         } else {
             red_add_f64(acc64 + 3 * gp + 0, (double)v);
             red_add_f64(acc64 + 3 * gp + 1, (double)(v * c));

@@ -8,6 +8,10 @@ maximum-likelihood estimator (P^T N^-1 P)^-1 P^T N^-1 d solved by PCG.
 """
 from __future__ import annotations
 
+import ctypes
+import json
+import math
+import os
 from dataclasses import dataclass, field
 
 import torch
@@ -284,18 +288,25 @@ class SolveInfo:
 def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64", acc="f32", inner_tol=1e-5,
                 max_outer=8, use_graph=True, check_every=10, rcond_min=1e-3, binned_only=False, hist_len=None,
                 out=None, true_residual=True, templates: "Templates | None" = None, amplitudes=None,
-                d_ready=None):
+                d_ready=None, allreduce=None):
     """Solve the map-making normal equations per observation; returns (map, valid mask, SolveInfo).
     With ``templates`` the system is the deprojected one (P^T F_T P) x = P^T F_T d; ``amplitudes``
     (float64 [ndet_total][order+1], optional) then receives the template amplitudes of the map.
     ``d_ready`` (a torch.cuda.Event recorded once d is written) lets the solver start its
-    preconditioner before d has arrived."""
+    preconditioner before d has arrived. ``allreduce`` (detector sharding: this process holds a
+    subset of the detectors of every observation) is fn(tensor), summing a CUDA tensor in place over
+    the processes, e.g. ``torch.distributed.all_reduce``; every process calls mapmaker_cg with the
+    same layout and gets the same map."""
     o = nat.default_cg_opts()
     o.maxiter, o.tol, o.precision, o.acc = int(maxiter), float(tol), _PREC[precision], _ACC[acc]
     o.inner_tol, o.max_outer, o.use_graph = float(inner_tol), int(max_outer), int(bool(use_graph))
     o.check_every, o.rcond_min, o.binned_only = int(check_every), float(rcond_min), int(bool(binned_only))
     o.true_residual = int(bool(true_residual))
     o.d_ready = None if d_ready is None else d_ready.cuda_event
+    cb = None
+    if allreduce is not None:
+        cb = nat.allreduce_callback(allreduce)
+        o.allreduce = ctypes.cast(cb, ctypes.c_void_p)
     x = out if out is not None else torch.empty(P.npix_total, 3, dtype=torch.float64, device=P.device)
     valid = torch.empty(P.npix_total, dtype=torch.uint8, device=P.device)
     hl = hist_len if hist_len is not None else maxiter + 1
@@ -305,6 +316,7 @@ def mapmaker_cg(P: Pointing, N: Noise, d, maxiter=50, tol=1e-8, precision="f64",
         rc, res, hist = nat.furax_mapmaker_cg_deproject(templates.handle, d.contiguous(), x, valid, o, hl, amplitudes)
     else:
         rc, res, hist = nat.furax_mapmaker_cg(P.handle, N.handle, d.contiguous(), x, valid, o, hl)
+    del cb
     return x, valid.bool(), SolveInfo(rc, res.iters, res.outer, res.rel_res, res.true_rel_res, res.n_valid, hist)
 
 
@@ -344,3 +356,59 @@ class Chi2(torch.autograd.Function):
 
 def chi2(m, psi_offset, P: Pointing, N: Noise, d, precision="f64"):
     return Chi2.apply(m, psi_offset, P, N, d, precision)
+
+
+_KERNELS = {0: "time_ordered", 1: "pixel_sorted"}
+
+
+def _tune_key(P: Pointing, N: "Noise", acc: str) -> str:
+    """Cache key of a tuned schedule: GPU, pixelisations, detectors, samples (power-of-two bucket),
+    pointing mode, noise kind and accumulation."""
+    name = torch.cuda.get_device_name(P.device)
+    bucket = int(round(math.log2(max(P.nsamp_total, 1))))
+    nsides = "/".join(str(n) for n in sorted(set(P.nside)))
+    return f"{name}|nside={nsides}|ndet={P.ndet_total}|nsamp=2^{bucket}|{P.mode}|{N.kind}|{acc}"
+
+
+def default_tune_cache() -> str:
+    return os.environ.get("FURAX_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "furax_gb300", "schedules.json"))
+
+
+def autotune(P: Pointing, N: "Noise", acc: str = "f32_kahan", reps: int = 3, cache_path: str | None = None,
+             candidates: list | None = None, retune: bool = False) -> dict:
+    """Pick the fastest schedule of the cached FP32 normal operator for this workload and set it on P.
+
+    The search (furax_autotune: each candidate timed on the GPU with CUDA events) runs once per key
+    of ``_tune_key``; the result is stored in a JSON file (``cache_path``, default
+    ``$FURAX_TUNE_CACHE`` or ``~/.cache/furax_gb300/schedules.json``) and later calls with the same
+    key set the stored schedule without timing. The accumulation mode is part of the key and is
+    never changed. Returns {"schedule", "ms", "cached", "key", "candidates_timed"}."""
+    path = cache_path or default_tune_cache()
+    key = _tune_key(P, N, acc)
+    table = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if not retune and key in table:
+        sch = table[key]["schedule"]
+        P.set_schedule(sch["kernel"], sch["tile_len"], sch["max_rows"], sch["group_tol"])
+        return {**table[key], "cached": True, "key": key}
+    space = candidates if candidates is not None else nat.furax_autotune_space()
+    ms, best = nat.furax_autotune(P.handle, N.handle, _ACC[acc], space, reps)
+    b = dict(space[best])
+    b["kernel"] = _KERNELS[int(b["kernel"])]
+    rec = {"schedule": b, "ms": ms[best], "candidates_timed": sum(1 for m in ms if m >= 0),
+           "times_ms": [[_KERNELS[int(c["kernel"])], c["tile_len"], c["max_rows"], c["group_tol"], m]
+                        for c, m in zip(space, ms)]}
+    table[key] = rec
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1)
+    os.replace(tmp, path)
+    return {**rec, "cached": False, "key": key}
+

@@ -13,6 +13,7 @@ HEADER = os.path.join(ROOT, "include", "furax.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src)   # function-pointer types are not entry points
     return sorted(set(re.findall(r"\b(furax_[a-z0-9_]+)\s*\(", src)))
 
 

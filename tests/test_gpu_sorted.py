@@ -95,7 +95,8 @@ def test_sorted_equals_time_ordered_to_rounding(fx, dev, batch):
     b = fx.ptnp_apply(P, N, xt, None, precision="f32", acc="f32_kahan")
     P.set_schedule("time_ordered")
     c = fx.ptnp_apply(P, N, xt, None, precision="f32", acc="f32_kahan")
-    assert torch.equal(a, c)
+    # compensated sums are order-independent to second order only (atomics land in any order)
+    assert rel(c, a, "time-ordered run to run") < 1e-9
     assert rel(b, a, "sorted vs time-ordered") < 1e-6
 
 
@@ -214,3 +215,29 @@ def test_schedule_validation(fx, dev):
     with pytest.raises(nat.FuraxError, match="FP32 pointing cache"):
         P64.set_schedule("pixel_sorted")
     P.close(); P64.close()
+
+
+def test_autotuned_schedule_keeps_oracle_parity_and_is_cached(fx, dev, orc, batch, tmp_path):
+    """The autotuner times candidate schedules on the handle's own workload (compensated
+    accumulation, never changed), leaves the fastest set, and stores it: the tuned operator stays
+    within the oracle bound, and a second call with the same key sets the stored schedule."""
+    obs, taps, sigma2, x, valid = batch
+    P = fx.Pointing.from_observations(obs, mode="cache_f32", device=dev)
+    N = fx.Noise.banded(P, taps)
+    space = fx._native.furax_autotune_space()
+    assert space[0]["kernel"] == 0 and len(space) > 10
+    cache = str(tmp_path / "schedules.json")
+    r = fx.autotune(P, N, "f32_kahan", reps=2, cache_path=cache, candidates=space[:1] + space[1::6])
+    assert not r["cached"] and r["candidates_timed"] >= 2
+    assert P.schedule()["kernel"] == r["schedule"]["kernel"]
+    got = fx.ptnp_apply(P, N, torch.as_tensor(np.concatenate(x), device=dev),
+                        torch.as_tensor(valid.astype(np.uint8), device=dev), precision="f32",
+                        acc="f32_kahan").cpu().numpy()
+    _check(orc, obs, _pts(P, obs), got, taps, sigma2, "banded", "f32_kahan", x, valid, "autotuned")
+    P.set_schedule("time_ordered")
+    r2 = fx.autotune(P, N, "f32_kahan", cache_path=cache)
+    assert r2["cached"] and r2["schedule"] == r["schedule"]
+    s = P.schedule()
+    assert (s["kernel"], s["tile_len"], s["max_rows"]) == (r["schedule"]["kernel"], r["schedule"]["tile_len"],
+                                                           r["schedule"]["max_rows"])
+    P.close()
