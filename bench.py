@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--tile-len", type=int, default=0)
     ap.add_argument("--max-rows", type=int, default=12)
     ap.add_argument("--group-tol", type=float, default=2.0)
+    ap.add_argument("--l2-evict-first", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--consumer-warps", type=int, default=0, choices=[0, 8, 16])
+    ap.add_argument("--no-tune", action="store_true", help="keep the default (time-ordered) schedule")
+    ap.add_argument("--tune-cache", default=None, help="JSON file of tuned schedules (default: the library's)")
     global ARGS
     ARGS = ap.parse_args()
     return ARGS
@@ -620,6 +624,11 @@ def batched_c4(fx, dev, stream, steps: int, joint: bool = False):
         P = fx.Pointing(qb, qd, nds, nss, nsides, mode="cache_f32", stream=stream,
                         map_id=nsides if joint else None)
         N = fx.Noise.banded(P, taps)
+        # a reduced search on the 9.75 G-sample batch (each sorted candidate sorts the whole batch):
+        # both kernels with their default tiles, with and without the L2 evict-first policy
+        space = [c for c in fx._native.furax_autotune_space()
+                 if c["kernel"] == 0 or (c["tile_len"] == 0 and c["max_rows"] == 12 and c["group_tol"] == 2.0)]
+        tune = fx.autotune(P, N, HEADLINE_ACC, reps=2, candidates=space)
         g = torch.Generator(device=dev).manual_seed(synth.SEED_BASE + 404)
         m = torch.randn(P.npix_total, 3, generator=g, device=dev, dtype=torch.float64)
         d = P.apply(m.float())
@@ -650,7 +659,8 @@ def batched_c4(fx, dev, stream, steps: int, joint: bool = False):
     ms = e0.elapsed_time(e1) / steps
     return {"workload": "64 observations, lengths uniform in [2^18, 2^22], 8-128 detectors, nside 256/512"
                         + (", one joint map per nside" if joint else ", one map per observation"),
-            "samples": S, "observations": 64, "maps": 2 if joint else 64, "apply_ms": apply_ms, "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
+            "samples": S, "observations": 64, "maps": 2 if joint else 64, "schedule": tune["schedule"],
+            "autotune_cached": tune["cached"], "apply_ms": apply_ms, "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
             "step_ms": ms, "value": S * CG_ITERS / (ms / 1e3) / 1e9, "unit": UNIT, "steps": steps}
 
 
@@ -815,9 +825,17 @@ def main():
     stream.synchronize()
     d_h = d.cpu().pin_memory()
 
+    # ---------------- schedule of the fused operator: the project's autotuner times the candidate
+    # schedules on this workload (not timed; cached per GPU and workload shape)
+    tune = None
+    if not args.apply_only and not args.no_tune:
+        with torch.cuda.stream(stream):
+            tune = fx.autotune(P, N, HEADLINE_ACC, reps=3, cache_path=args.tune_cache)
+
     if args.apply_only:
         if args.schedule:
-            P.set_schedule(args.schedule, tile_len=args.tile_len, max_rows=args.max_rows, group_tol=args.group_tol)
+            P.set_schedule(args.schedule, tile_len=args.tile_len, max_rows=args.max_rows, group_tol=args.group_tol,
+                           l2_evict_first=args.l2_evict_first, consumer_warps=args.consumer_warps)
         xin = torch.randn(npix, 3, dtype=torch.float64, device=dev, generator=g)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
@@ -918,7 +936,9 @@ def main():
         "data": "synthetic (seeded satellite scan, Gaussian sky, FFT-shaped 1/f noise)",
         "config": {"workload": _wl_name(wl), **wl, "cg_iters": CG_ITERS, "pointing": "expanded each step from FP64 "
                    "quaternions into an FP32 cache", "accumulation": f"{HEADLINE_ACC} (compensated FP32 per pixel)",
-                   "l2": "inputs larger than L2 (3.2 GB pointing cache streamed per apply)"},
+                   "schedule": P.schedule(), "l2": "inputs larger than L2 (3.2 GB pointing cache streamed per apply)"},
+        "autotune": None if tune is None else {k: tune[k] for k in ("schedule", "ms", "cached", "key",
+                                                                     "candidates_timed")},
         "roofline": roofline,
         "apply_gsamples_per_s": S / (apply_ms / 1e3) / 1e9,
         "fp64_fused_ms_per_launch": (f64_ms / f64_n) if f64_n else None,

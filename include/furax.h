@@ -100,6 +100,11 @@ typedef struct {
                            many as the tile's stage holds for its rows */
     int32_t max_rows;   /* pixel-sorted: detectors per tile, 1..16 */
     double group_tol;   /* pixel-sorted: cross-scan grouping tolerance in pixel widths (> 0) */
+    int32_t l2_evict_first; /* both kernels: 1 reads the pointing stream (read once per application)
+                               with an L2 evict-first policy, so that it does not evict the map and
+                               the accumulators; 0 uses the default policy */
+    int32_t consumer_warps; /* time-ordered kernel: warps that run the band and the scatter, 8 or 16
+                               (0 = 8); with 16 twice the reductions are in flight (templates keep 8) */
 } furax_schedule;
 
 /* A batch of observations: each with its own map, or sharing maps by map_id. */
@@ -171,8 +176,9 @@ furax_status furax_pointing_get_schedule(const furax_pointing_t *p, furax_schedu
 furax_status furax_autotune(furax_pointing_t *p, const furax_noise_t *n, int32_t acc, const furax_schedule *cand,
                             int32_t ncand, int32_t reps, double *ms_out, int32_t *best_out, void *stream);
 /* The built-in search space: copies up to cap candidates into out (may be NULL) and returns how
- * many there are: the time-ordered kernel, then the pixel-sorted kernel over tile_len
- * {0, 128, 256, 512} x max_rows {4, 8, 12, 16} x group_tol {1, 2, 4}. */
+ * many there are: for l2_evict_first 0 and 1, the time-ordered kernel with 8 and 16 consumer
+ * warps, then the pixel-sorted kernel over tile_len {0, 256, 512} x max_rows {8, 12} x
+ * group_tol {1, 2}. */
 int32_t furax_autotune_space(furax_schedule *out, int32_t cap);
 
 /* Replace the per-detector polarisation-angle offsets (device [sum ndet] rad, or NULL for none).

@@ -75,7 +75,7 @@ def allreduce_callback(fn):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("tile_len", ctypes.c_int32), ("max_rows", ctypes.c_int32),
-                ("group_tol", ctypes.c_double)]
+                ("group_tol", ctypes.c_double), ("l2_evict_first", ctypes.c_int32), ("consumer_warps", ctypes.c_int32)]
 
 
 FURAX_SCHED_TIME_ORDERED, FURAX_SCHED_PIXEL_SORTED = 0, 1
@@ -259,28 +259,32 @@ def furax_device_status(h, stream=None) -> None:
 
 
 def furax_pointing_set_schedule(h, kernel: int, tile_len: int = 0, max_rows: int = 12, group_tol: float = 2.0,
-                                stream=None) -> None:
-    sch = Schedule(int(kernel), int(tile_len), int(max_rows), float(group_tol))
+                                l2_evict_first: int = 0, consumer_warps: int = 0, stream=None) -> None:
+    sch = Schedule(int(kernel), int(tile_len), int(max_rows), float(group_tol), int(l2_evict_first),
+                   int(consumer_warps))
     _call("furax_pointing_set_schedule", h, ctypes.byref(sch), _stream(stream))
 
 
 def furax_pointing_get_schedule(h) -> dict:
     sch = Schedule()
     _call("furax_pointing_get_schedule", h, ctypes.byref(sch))
-    return dict(kernel=sch.kernel, tile_len=sch.tile_len, max_rows=sch.max_rows, group_tol=sch.group_tol)
+    return dict(kernel=sch.kernel, tile_len=sch.tile_len, max_rows=sch.max_rows, group_tol=sch.group_tol,
+                l2_evict_first=sch.l2_evict_first, consumer_warps=sch.consumer_warps)
 
 
 def furax_autotune_space() -> list:
     n = lib().furax_autotune_space(None, 0)
     arr = (Schedule * n)()
     lib().furax_autotune_space(arr, n)
-    return [dict(kernel=c.kernel, tile_len=c.tile_len, max_rows=c.max_rows, group_tol=c.group_tol) for c in arr]
+    return [dict(kernel=c.kernel, tile_len=c.tile_len, max_rows=c.max_rows, group_tol=c.group_tol,
+                 l2_evict_first=c.l2_evict_first, consumer_warps=c.consumer_warps) for c in arr]
 
 
 def furax_autotune(hp, hn, acc: int, candidates: list, reps: int = 3, stream=None):
     """Time each candidate schedule (dicts of furax_schedule fields); returns (ms per candidate, best index)."""
     n = len(candidates)
-    arr = (Schedule * n)(*[Schedule(int(c["kernel"]), int(c["tile_len"]), int(c["max_rows"]), float(c["group_tol"]))
+    arr = (Schedule * n)(*[Schedule(int(c["kernel"]), int(c["tile_len"]), int(c["max_rows"]), float(c["group_tol"]),
+                                    int(c.get("l2_evict_first", 0)), int(c.get("consumer_warps", 0)))
                            for c in candidates])
     ms = (ctypes.c_double * n)()
     best = _I32()

@@ -11,16 +11,20 @@
 
 namespace fx {
 
-// The built-in search space: the time-ordered kernel, then the pixel-sorted kernel over tile
+// The built-in search space, with and without the L2 evict-first policy on the pointing stream:
+// the time-ordered kernel with 8 or 16 consumer warps, then the pixel-sorted kernel over tile
 // length (0 = the largest the stage holds for the tile's rows), detectors per tile and the
 // cross-scan grouping tolerance in pixel widths.
 static std::vector<furax_schedule> default_space()
 {
     std::vector<furax_schedule> v;
-    v.push_back(furax_schedule{FURAX_SCHED_TIME_ORDERED, 0, 1, 1.0});
-    for (int tl : {0, 128, 256, 512})
-        for (int rows : {4, 8, 12, 16})
-            for (double tol : {1.0, 2.0, 4.0}) v.push_back(furax_schedule{FURAX_SCHED_PIXEL_SORTED, tl, rows, tol});
+    for (int hint : {0, 1}) {
+        for (int kc : {8, 16}) v.push_back(furax_schedule{FURAX_SCHED_TIME_ORDERED, 0, 1, 1.0, hint, kc});
+        for (int tl : {0, 256, 512})
+            for (int rows : {8, 12})
+                for (double tol : {1.0, 2.0})
+                    v.push_back(furax_schedule{FURAX_SCHED_PIXEL_SORTED, tl, rows, tol, hint, 0});
+    }
     return v;
 }
 

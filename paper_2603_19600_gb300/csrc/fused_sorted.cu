@@ -66,14 +66,6 @@ __device__ __forceinline__ void smbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ void sbulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
 __device__ __forceinline__ bool sconsumers_all(bool ok)
 {
     int r;
@@ -197,7 +189,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
     fused_sorted_kernel(const STile *__restrict__ tiles, int64_t n_tiles, const int32_t *__restrict__ sdet,
                         const uint16_t *__restrict__ perm, const int32_t *__restrict__ perm_n, PointingView pv,
                         NoiseView nv, const float4 *__restrict__ x32, float4 *__restrict__ acc_hi,
-                        float4 *__restrict__ acc_lo, double *__restrict__ acc64, unsigned *__restrict__ err)
+                        float4 *__restrict__ acc_lo, double *__restrict__ acc64, unsigned *__restrict__ err,
+                        int l2_hint)
 {
     extern __shared__ __align__(128) unsigned char ssm[];
     SortedSmem &S = *reinterpret_cast<SortedSmem *>(ssm);
@@ -218,6 +211,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
         // ---------------- loader: rows' pixels and weights (with halos) and the tile's permutation
         if ((threadIdx.x & 31) != 0) return;
         if (loader_held(err)) return;
+        const bool hint = l2_hint != 0;   // the pointing stream and permutation are read once
+        const uint64_t pol = hint ? evict_first_policy() : 0ull;
         int64_t it = 0;
         for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
             const int r = (int)(it & 1);
@@ -239,11 +234,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
             for (int row = 0; row < tl.nrow; ++row) {
                 const SRowSpan sp = srow_span(tl, ob, sdet[tl.det0 + row]);
                 const uint32_t nb = 4u * (uint32_t)sp.n;
-                sbulk_g2s(&S.pix[r][row * rs], pv.pix + sp.g0, nb, &S.raw_full[r]);
-                sbulk_g2s(&S.c[r][row * rs], pv.c32 + sp.g0, nb, &S.raw_full[r]);
-                sbulk_g2s(&S.s[r][row * rs], pv.s32 + sp.g0, nb, &S.raw_full[r]);
+                bulk_copy_g2s(&S.pix[r][row * rs], pv.pix + sp.g0, nb, &S.raw_full[r], hint, pol);
+                bulk_copy_g2s(&S.c[r][row * rs], pv.c32 + sp.g0, nb, &S.raw_full[r], hint, pol);
+                bulk_copy_g2s(&S.s[r][row * rs], pv.s32 + sp.g0, nb, &S.raw_full[r], hint, pol);
             }
-            if (pbytes) sbulk_g2s(S.perm[r], perm + tl.perm_off, pbytes, &S.raw_full[r]);
+            if (pbytes) bulk_copy_g2s(S.perm[r], perm + tl.perm_off, pbytes, &S.raw_full[r], hint, pol);
         }
         for (int64_t j = it - 1; j >= 0 && j >= it - 2; --j)
             mbar_wait(&S.raw_full[j & 1], (uint32_t)((j >> 1) & 1), err, budget);
@@ -467,6 +462,9 @@ furax_status set_schedule(furax_pointing *p, const furax_schedule &s, cudaStream
 {
     if (s.kernel != FURAX_SCHED_TIME_ORDERED && s.kernel != FURAX_SCHED_PIXEL_SORTED)
         return set_error(FURAX_EINVAL, "unknown schedule kernel %d", s.kernel);
+    if (s.l2_evict_first != 0 && s.l2_evict_first != 1) return set_error(FURAX_EINVAL, "l2_evict_first must be 0 or 1");
+    if (s.consumer_warps != 0 && s.consumer_warps != 8 && s.consumer_warps != 16)
+        return set_error(FURAX_EINVAL, "consumer_warps must be 0, 8 or 16");
     if (s.kernel == FURAX_SCHED_PIXEL_SORTED) {
         if (p->mode != FURAX_POINTING_CACHE_F32 && p->mode != FURAX_POINTING_CACHE_MIXED)
             return set_error(FURAX_EINVAL, "the pixel-sorted schedule needs the FP32 pointing cache");
@@ -627,7 +625,8 @@ static furax_status run_sorted(const furax_pointing *p, const furax_noise *n, co
 {
     const unsigned g = (unsigned)std::min<int64_t>(p->n_stiles, p->n_sm);
     return launch_dyn(fused_sorted_kernel<ACC, BANDED>, g, kSThreads, kSortedSmem, st, p->d_stiles, p->n_stiles,
-                      p->d_sdet, p->d_perm, p->d_perm_n, p->view(), n->view(), x32, hi, lo, a64, p->d_err);
+                      p->d_sdet, p->d_perm, p->d_perm_n, p->view(), n->view(), x32, hi, lo, a64, p->d_err,
+                      (int)p->sched.l2_evict_first);
 }
 
 template <bool BANDED>

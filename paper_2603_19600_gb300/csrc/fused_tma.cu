@@ -28,9 +28,11 @@
 namespace fx {
 
 constexpr int kTmaGather = 7;                      // gather warps
-constexpr int kTmaConsumer = 8;                    // consumer warps
-constexpr int kConsOut = TILE / (32 * kTmaConsumer);   // consecutive outputs per consumer thread
-constexpr int kTmaThreads = 32 * (kTmaGather + kTmaConsumer + 1);
+// Consumer warps KC (a template parameter: 8 or 16, chosen by the schedule): each consumer thread
+// owns TILE / (32 KC) consecutive outputs of the band; with 16 the scatter has twice the
+// threads (and returning atomics) in flight and the band product half the outputs per thread.
+template <int KC> constexpr int cons_out() { return TILE / (32 * KC); }
+template <int KC> constexpr int tma_threads() { return 32 * (kTmaGather + KC + 1); }
 constexpr int kRawStages = 2;
 constexpr int kXsStages = 2;
 // Elements of one pointing stream copied per tile: tile + halos, widened to 16-byte boundaries.
@@ -38,7 +40,8 @@ constexpr int kRawN = 4232;
 static_assert(kRawN % 4 == 0 && kRawN >= TILE + 2 * kHalo + 6, "raw stage must hold an aligned tile + halos");
 constexpr int kGatherPer = (TILE + 2 * kHalo + 32 * kTmaGather - 1) / (32 * kTmaGather);
 constexpr int kKahanBatch = 4;                     // returning atomics in flight per consumer thread
-static_assert(kConsOut % kKahanBatch == 0, "Kahan batches tile a thread's outputs");
+static_assert(cons_out<16>() % kKahanBatch == 0 && cons_out<8>() % kKahanBatch == 0,
+              "Kahan batches tile a thread's outputs");
 
 struct TmaSmem {
     int32_t pix[kRawStages][kRawN];
@@ -72,7 +75,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-// AND of `ok` over the 256 consumer threads (named barrier 1); every consumer thread must call it.
+// AND of `ok` over the 32 KC consumer threads (named barrier 1); every consumer thread must call it.
+template <int KC>
 __device__ __forceinline__ bool consumers_all(bool ok)
 {
     int r;
@@ -82,14 +86,15 @@ __device__ __forceinline__ bool consumers_all(bool ok)
         "bar.red.and.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((unsigned)ok), "n"(32 * kTmaConsumer)
+        : "r"((unsigned)ok), "n"(32 * KC)
         : "memory");
     return r != 0;
 }
 
+template <int KC>
 __device__ __forceinline__ void consumers_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kTmaConsumer) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * KC) : "memory");
 }
 
 // Tile geometry in the flat cache: the copied range [g0, g0 + n) covers every in-stream sample
@@ -118,12 +123,14 @@ __device__ __forceinline__ TileSpan tile_span(const Tile &tl, const ObsInfo &ob,
 //   TPL 2: the augmented system [m; a]: u_t = (P m)_t + sum_l a_l P_l(tau_t) with the detector's
 //          amplitudes a (l <= 2) read from x32[tpl.base + det], and T^T z (l <= tpl.order)
 //          accumulated into the amplitude pseudo-pixel tpl.base + det like a pixel.
-template <int ACC, bool BANDED, int TPL>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+template <int ACC, bool BANDED, int TPL, int KC>
+__global__ void __launch_bounds__(tma_threads<KC>(), 1)
     fused_tma_kernel(const Tile *__restrict__ tiles, int64_t n_tiles, PointingView pv, NoiseView nv,
                      const float4 *__restrict__ x32, float4 *__restrict__ acc_hi, float4 *__restrict__ acc_lo,
-                     double *__restrict__ acc64, unsigned *__restrict__ err, FusedTpl tpl)
+                     double *__restrict__ acc64, unsigned *__restrict__ err, FusedTpl tpl, int l2_hint)
 {
+    constexpr int kTmaConsumer = KC;
+    constexpr int kConsOut = cons_out<KC>();
     extern __shared__ __align__(128) unsigned char tsm[];
     TmaSmem &S = *reinterpret_cast<TmaSmem *>(tsm);
     constexpr int halo = BANDED ? kHalo : 0;
@@ -141,6 +148,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if ((threadIdx.x & 31) != 0) return;
         // held (test hook): issue nothing; the gather and consumer waits then run out
         if (loader_held(err)) return;
+        const bool hint = l2_hint != 0;   // the pointing stream is read once: evict it first
+        const uint64_t pol = hint ? evict_first_policy() : 0ull;
         int64_t it = 0;
         for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, ++it) {
             const int r = (int)(it % kRawStages);
@@ -151,9 +160,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const TileSpan sp = tile_span(tl, ob, halo);
             const uint32_t bytes = (uint32_t)sp.n * 4u;
             mbar_expect_tx(&S.raw_full[r], 3u * bytes + (TPL == 2 ? (uint32_t)sizeof(float4) : 0u));
-            bulk_g2s(S.pix[r], pv.pix + sp.g0, bytes, &S.raw_full[r]);
-            bulk_g2s(S.c[r], pv.c32 + sp.g0, bytes, &S.raw_full[r]);
-            bulk_g2s(S.s[r], pv.s32 + sp.g0, bytes, &S.raw_full[r]);
+            bulk_copy_g2s(S.pix[r], pv.pix + sp.g0, bytes, &S.raw_full[r], hint, pol);
+            bulk_copy_g2s(S.c[r], pv.c32 + sp.g0, bytes, &S.raw_full[r], hint, pol);
+            bulk_copy_g2s(S.s[r], pv.s32 + sp.g0, bytes, &S.raw_full[r], hint, pol);
             // the tile detector's amplitudes ride on the same barrier (16 bytes, 16-byte aligned)
             if constexpr (TPL == 2)
                 bulk_g2s(&S.amp[r], x32 + tpl.base + ob.det_off + tl.det, (uint32_t)sizeof(float4), &S.raw_full[r]);
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         }
         // Every consumer has read its stencil inputs: y overwrites the stage in place (core
         // sample u at slot spos(u)), which is released to the gathers after the scatter.
-        if (!consumers_all(ok)) break;
+        if (!consumers_all<KC>(ok)) break;
         if constexpr (TPL != 0) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             if (base < tl.len) {
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
         for (int i = 0; i < kConsOut; ++i)
             if (base + i < tl.len) ys[spos(base + i)] = y[i];
-        consumers_sync();
+        consumers_sync<KC>();
         const TileSpan sp = tile_span(tl, ob, halo);
         const int64_t shift = sp.row + tl.t0 - sp.g0;   // stage index of core sample u
         double2 cs = make_double2(1.0, 0.0);
@@ -354,13 +363,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 }
 
+template <int ACC, bool BANDED, int TPL, int KC>
+static furax_status run_tma_kc(const furax_pointing *p, const furax_noise *n, const float4 *x32, float4 *hi,
+                               float4 *lo, double *a64, const FusedTpl &ft, cudaStream_t st)
+{
+    const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
+    return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL, KC>, g, tma_threads<KC>(), kTmaSmem, st, p->d_tiles,
+                      p->n_tiles, p->view(), n->view(), x32, hi, lo, a64, p->d_err, ft, (int)p->sched.l2_evict_first);
+}
+
+// 16 consumer warps when the schedule asks for them (plain operator only; the template modes keep 8).
 template <int ACC, bool BANDED, int TPL>
 static furax_status run_tma(const furax_pointing *p, const furax_noise *n, const float4 *x32, float4 *hi, float4 *lo,
                             double *a64, const FusedTpl &ft, cudaStream_t st)
 {
-    const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
-    return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL>, g, kTmaThreads, kTmaSmem, st, p->d_tiles, p->n_tiles,
-                      p->view(), n->view(), x32, hi, lo, a64, p->d_err, ft);
+    if constexpr (TPL == 0)
+        if (p->sched.consumer_warps == 16) return run_tma_kc<ACC, BANDED, TPL, 16>(p, n, x32, hi, lo, a64, ft, st);
+    return run_tma_kc<ACC, BANDED, TPL, 8>(p, n, x32, hi, lo, a64, ft, st);
 }
 
 template <bool BANDED, int TPL>
@@ -389,25 +408,27 @@ furax_status launch_fused_tma(const furax_pointing *p, const furax_noise *n, con
     return dispatch_tma_band<2>(p, n, x32, acc, hi, lo, a64, *ft, st);
 }
 
-template <bool BANDED, int TPL>
+template <bool BANDED, int TPL, int KC>
 static furax_status prepare_tma_band()
 {
     furax_status rc = FURAX_OK;
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, BANDED, TPL>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, BANDED, TPL>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, BANDED, TPL>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, BANDED, TPL, KC>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, BANDED, TPL, KC>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, BANDED, TPL, KC>, kTmaSmem);
     return rc;
 }
 
 furax_status prepare_fused_tma()
 {
     furax_status rc = FURAX_OK;
-    if (!rc) rc = prepare_tma_band<true, 0>();
-    if (!rc) rc = prepare_tma_band<false, 0>();
-    if (!rc) rc = prepare_tma_band<true, 1>();
-    if (!rc) rc = prepare_tma_band<false, 1>();
-    if (!rc) rc = prepare_tma_band<true, 2>();
-    if (!rc) rc = prepare_tma_band<false, 2>();
+    if (!rc) rc = prepare_tma_band<true, 0, 8>();
+    if (!rc) rc = prepare_tma_band<false, 0, 8>();
+    if (!rc) rc = prepare_tma_band<true, 0, 16>();
+    if (!rc) rc = prepare_tma_band<false, 0, 16>();
+    if (!rc) rc = prepare_tma_band<true, 1, 8>();
+    if (!rc) rc = prepare_tma_band<false, 1, 8>();
+    if (!rc) rc = prepare_tma_band<true, 2, 8>();
+    if (!rc) rc = prepare_tma_band<false, 2, 8>();
     return rc;
 }
 

@@ -598,11 +598,13 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
             return rc;
     }
     if (e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    int acc_q = acc;   // where cg_q reads the operator's output
     if (b.ar.on()) {
         // detector sharding: this process's partial P^T N^-1 P p, in FP64, summed over processes
+        // (the FP32 accumulators are still cleared for the next application below)
         if (acc != FURAX_ACC_F64) {
             if ((rc = launch_finalize_acc(p, acc, w->hi, w->lo, nullptr, nullptr, w->acc64, st))) return rc;
-            acc = FURAX_ACC_F64;
+            acc_q = FURAX_ACC_F64;
         }
         if ((rc = b.ar(w->acc64, 3 * p->npix_total, FURAX_REDUCE_F64, st))) return rc;
     }
@@ -612,7 +614,7 @@ static furax_status body(const Body &b, cudaStream_t st, cudaEvent_t e0, cudaEve
                                  !f64 && tpl_fused_target(b.tp, p) != nullptr)))
             return rc;
     }
-    cg_q_kernel<<<b.pg, VT, 0, st>>>(b.pt, acc, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
+    cg_q_kernel<<<b.pg, VT, 0, st>>>(b.pt, acc_q, w->hi, w->lo, w->acc64, w->valid, w->p, w->q, w->partial);
     cg_alpha_kernel<<<p->n_obs, VT, 0, st>>>(b.cobs, w->partial, w->sc);
     cg_update_kernel<<<b.pg, VT, 0, st>>>(b.pt, w->sc, w->minv, w->valid, b.x, w->r, w->z, w->p, w->q, w->partial);
     cg_beta_kernel<<<p->n_obs, VT, 0, st>>>(b.cobs, w->partial, w->sc, b.tol2, w->hist, w->hist_cap);

@@ -89,13 +89,15 @@ class Pointing:
         except Exception:
             pass
 
-    def set_schedule(self, kernel="time_ordered", tile_len=0, max_rows=12, group_tol=2.0):
+    def set_schedule(self, kernel="time_ordered", tile_len=0, max_rows=12, group_tol=2.0, l2_evict_first=0,
+                     consumer_warps=0):
         """How the cached FP32 normal operator walks the samples: "time_ordered" (one detector x
         4096 samples per tile) or "pixel_sorted" (detectors on one track x tile_len samples, samples
-        sorted by pixel once per refresh; see furax_schedule). Only the order of the floating-point
-        additions changes."""
+        sorted by pixel once per refresh; see furax_schedule); l2_evict_first=1 reads the pointing
+        stream with an L2 evict-first policy; consumer_warps (8 or 16, time-ordered kernel) sets how many
+        warps run the band and the scatter. Only the order of the floating-point additions changes."""
         k = {"time_ordered": nat.FURAX_SCHED_TIME_ORDERED, "pixel_sorted": nat.FURAX_SCHED_PIXEL_SORTED}[kernel]
-        nat.furax_pointing_set_schedule(self.handle, k, tile_len, max_rows, group_tol)
+        nat.furax_pointing_set_schedule(self.handle, k, tile_len, max_rows, group_tol, l2_evict_first, consumer_warps)
 
     def schedule(self) -> dict:
         s = nat.furax_pointing_get_schedule(self.handle)
@@ -395,14 +397,16 @@ def autotune(P: Pointing, N: "Noise", acc: str = "f32_kahan", reps: int = 3, cac
             table = {}
     if not retune and key in table:
         sch = table[key]["schedule"]
-        P.set_schedule(sch["kernel"], sch["tile_len"], sch["max_rows"], sch["group_tol"])
+        P.set_schedule(sch["kernel"], sch["tile_len"], sch["max_rows"], sch["group_tol"], sch.get("l2_evict_first", 0),
+                       sch.get("consumer_warps", 0))
         return {**table[key], "cached": True, "key": key}
     space = candidates if candidates is not None else nat.furax_autotune_space()
     ms, best = nat.furax_autotune(P.handle, N.handle, _ACC[acc], space, reps)
     b = dict(space[best])
     b["kernel"] = _KERNELS[int(b["kernel"])]
     rec = {"schedule": b, "ms": ms[best], "candidates_timed": sum(1 for m in ms if m >= 0),
-           "times_ms": [[_KERNELS[int(c["kernel"])], c["tile_len"], c["max_rows"], c["group_tol"], m]
+           "times_ms": [[_KERNELS[int(c["kernel"])], c["tile_len"], c["max_rows"], c["group_tol"],
+                         int(c.get("l2_evict_first", 0)), int(c.get("consumer_warps", 0)), m]
                         for c, m in zip(space, ms)]}
     table[key] = rec
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)

@@ -38,7 +38,7 @@ def main():
         dist.all_reduce(host)
         t.copy_(host)
 
-    x, v, info = fx.mapmaker_cg(P, N, d, maxiter=400, tol=1e-10, precision=precision, acc="f32_kahan",
+    x, v, info = fx.mapmaker_cg(P, N, d, maxiter=600, tol=1e-12, precision=precision, acc="f32_kahan",
                                 allreduce=allreduce)
     np.save(os.path.join(work, f"x{rank}.npy"), x.cpu().numpy())
     np.save(os.path.join(work, f"v{rank}.npy"), v.cpu().numpy())

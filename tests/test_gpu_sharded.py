@@ -50,7 +50,9 @@ def test_sharded_solve_equals_joint_solve_and_oracle(fx, dev, orc, tmp_path, pre
     # the single-process solve over all detectors
     P = fx.Pointing.from_observations([o], mode=mode, device=dev)
     N = fx.Noise.banded(P, taps)
-    x, v, info = fx.mapmaker_cg(P, N, torch.as_tensor(d.ravel(), device=dev), maxiter=400, tol=1e-10,
+    # both solved to 1e-12, as the oracle: the stopping point then does not decide the per-component
+    # comparison (Q and U are ~100 times smaller than I)
+    x, v, info = fx.mapmaker_cg(P, N, torch.as_tensor(d.ravel(), device=dev), maxiter=600, tol=1e-12,
                                 precision=precision, acc="f32_kahan")
     assert info.converged
     v = v.cpu().numpy()

@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
 SHAPES = [(24, 66536, 128), (17, 40003, 64), (23, 70001, 128)]   # > 4 tiles per CTA either way
-SCHEDULES = [dict(), dict(tile_len=64, max_rows=4, group_tol=0.5), dict(tile_len=1024, max_rows=3, group_tol=4.0)]
+SCHEDULES = [dict(), dict(tile_len=64, max_rows=4, group_tol=0.5), dict(tile_len=1024, max_rows=3, group_tol=4.0),
+             dict(l2_evict_first=1)]
 
 
 def _pts(P, obs):
@@ -80,6 +81,24 @@ def test_sorted_operator_matches_oracle(fx, dev, orc, batch, sched, kind, acc):
     got = fx.ptnp_apply(P, N, torch.as_tensor(np.concatenate(x), device=dev),
                         torch.as_tensor(valid.astype(np.uint8), device=dev), precision="f32", acc=acc).cpu().numpy()
     _check(orc, obs, _pts(P, obs), got, taps, sigma2, kind, acc, x, valid, f"sorted{sched}/{kind}/{acc}")
+    P.close()
+
+
+@pytest.mark.parametrize("kind", ["banded", "white"])
+@pytest.mark.parametrize("acc", ["f32_kahan", "f32"])
+@pytest.mark.parametrize("kc", [8, 16])
+def test_time_ordered_schedules_match_oracle(fx, dev, orc, batch, kind, acc, kc):
+    """The L2 evict-first policy on the pointing stream changes only where data are cached; 16
+    consumer warps (8 outputs and twice the reductions in flight per thread block) only the split
+    of the work."""
+    obs, taps, sigma2, x, valid = batch
+    P = fx.Pointing.from_observations(obs, mode="cache_f32", device=dev)
+    P.set_schedule("time_ordered", l2_evict_first=1, consumer_warps=kc)
+    assert P.schedule()["l2_evict_first"] == 1 and P.schedule()["consumer_warps"] == kc
+    N = fx.Noise.banded(P, taps) if kind == "banded" else fx.Noise.white(P, sigma2)
+    got = fx.ptnp_apply(P, N, torch.as_tensor(np.concatenate(x), device=dev),
+                        torch.as_tensor(valid.astype(np.uint8), device=dev), precision="f32", acc=acc).cpu().numpy()
+    _check(orc, obs, _pts(P, obs), got, taps, sigma2, kind, acc, x, valid, f"time-ordered l2 kc{kc}/{kind}/{acc}")
     P.close()
 
 
@@ -205,7 +224,8 @@ def test_schedule_validation(fx, dev):
     o = synth.Observation(8, synth.satellite_scan(5000), synth.hex_focal_plane(4))
     P = fx.Pointing.from_observations([o], mode="cache_f32", device=dev)
     assert P.schedule()["kernel"] == "time_ordered"
-    for bad in (dict(tile_len=24), dict(tile_len=8192), dict(max_rows=0), dict(max_rows=17), dict(group_tol=0.0)):
+    for bad in (dict(tile_len=24), dict(tile_len=8192), dict(max_rows=0), dict(max_rows=17), dict(group_tol=0.0),
+                dict(l2_evict_first=2), dict(consumer_warps=12)):
         with pytest.raises(nat.FuraxError):
             P.set_schedule("pixel_sorted", **bad)
     P.set_schedule("pixel_sorted", tile_len=128, max_rows=5, group_tol=1.5)
