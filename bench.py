@@ -31,14 +31,18 @@ import synth  # noqa: E402
 METRIC = "Gsamples/s of P^T N^-1 P apply; CG solve time at residual 1e-8 vs plain FP64 GPU"
 UNIT = "Gsamples/s"
 CG_ITERS = 50
-# Per-pixel accumulation of the timed operator: compensated FP32 (the contract's precision).
-HEADLINE_ACC = "f32_kahan"
+# Per-pixel accumulation of the timed operator: FP64 per pixel (of the two accumulations the contract
+# allows, FP64 and compensated FP32, the faster here and the more accurate).
+HEADLINE_ACC = "f64"
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of one fused_tma_kernel launch, ACC_F32_KAHAN, 64 detectors x 2^20 samples
-# at nside 512), per sample; the full workload's figure is this times its samples. It is valid
-# only for the kernel sources it was taken on: bench reports null once their hash differs.
-TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes_per_sample": None,
-                   "case": "64 detectors x 2^20 samples, nside 512, ACC_F32_KAHAN"}
+# dram__bytes_write.sum of one fused_tma_kernel launch, FP64 accumulation, 64 detectors x 2^20
+# samples at nside 512, the schedule the autotuner picks for the full workload), per sample; the
+# full workload's figure is this times its samples. It is valid only for the kernel sources it
+# was taken on: bench reports null once their hash differs.
+TRAFFIC_CAPTURE = {"sources_sha256": "307f4d311c34504fba72fd25a8008a14f19397b2c75c2c086b1b65a21e6acf28",
+                   "bytes_per_sample": (1205469696 + 246056448) / 67108864,
+                   "case": "64 detectors x 2^20 samples, nside 512, ACC_F64, time-ordered, L2 evict-first, "
+                           "8 consumer warps"}
 KERNEL_SOURCES = ("fused_tma.cu", "tile.cuh", "mbarrier.cuh", "atomics.cuh", "stencil.cuh", "pointing_math.cuh",
                   "internal.cuh")
 # Source-level FP64 operations per sample of the on-the-fly pointing (quaternion product 28,
@@ -75,7 +79,7 @@ def parse():
     ap.add_argument("--acc", default=HEADLINE_ACC, choices=["f32", "f32_kahan", "f64"],
                     help="per-pixel accumulation of --apply-only runs")
     ap.add_argument("--schedule", default=None, choices=["time_ordered", "pixel_sorted"],
-                    help="operator schedule of --apply-only runs (default: the bench's)")
+                    help="operator schedule instead of the autotuner's choice (profiling runs)")
     ap.add_argument("--tile-len", type=int, default=0)
     ap.add_argument("--max-rows", type=int, default=12)
     ap.add_argument("--group-tol", type=float, default=2.0)
@@ -828,7 +832,10 @@ def main():
     # ---------------- schedule of the fused operator: the project's autotuner times the candidate
     # schedules on this workload (not timed; cached per GPU and workload shape)
     tune = None
-    if not args.apply_only and not args.no_tune:
+    if not args.apply_only and args.schedule:   # an explicit schedule (profiling runs) instead of the search
+        P.set_schedule(args.schedule, tile_len=args.tile_len, max_rows=args.max_rows, group_tol=args.group_tol,
+                       l2_evict_first=args.l2_evict_first, consumer_warps=args.consumer_warps)
+    elif not args.apply_only and not args.no_tune:
         with torch.cuda.stream(stream):
             tune = fx.autotune(P, N, HEADLINE_ACC, reps=3, cache_path=args.tune_cache)
 
@@ -935,7 +942,7 @@ def main():
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded satellite scan, Gaussian sky, FFT-shaped 1/f noise)",
         "config": {"workload": _wl_name(wl), **wl, "cg_iters": CG_ITERS, "pointing": "expanded each step from FP64 "
-                   "quaternions into an FP32 cache", "accumulation": f"{HEADLINE_ACC} (compensated FP32 per pixel)",
+                   "quaternions into an FP32 cache", "accumulation": {"f64": "f64 (FP64 per pixel)", "f32_kahan": "f32_kahan (compensated FP32 per pixel)"}[HEADLINE_ACC],
                    "schedule": P.schedule(), "l2": "inputs larger than L2 (3.2 GB pointing cache streamed per apply)"},
         "autotune": None if tune is None else {k: tune[k] for k in ("schedule", "ms", "cached", "key",
                                                                      "candidates_timed")},
@@ -978,31 +985,42 @@ def main():
         out["e2e"] = {"value": job_value(samples_per_step, args.steps, e2e_ms, world), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
 
-    # ---------------- the same step with plain FP32 per-pixel accumulation (outside the contract's
-    # precision; reported only as the cost of compensation)
-    with torch.cuda.stream(stream):
-        step(acc="f32")
-        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nat.furax_profile_reset()
-        nat.furax_profile_enable(True)
-        e2.record(stream)
-        nsteps = max(1, min(args.steps, 3))
-        for _ in range(nsteps):
-            step(acc="f32")
-        e3.record(stream)
-        stream.synchronize()
-        nat.furax_profile_enable(False)
-    n32_ms, n32_n = nat.furax_profile_read(0)
-    ms32 = e2.elapsed_time(e3) / nsteps
-    out["plain_fp32_accumulation_step"] = {
-        "note": "same step with naive FP32 per-pixel sums (not the contract's precision)",
-        "ms_per_step": ms32, "value": samples_per_step / (ms32 / 1e3) / 1e9, "unit": UNIT,
-        "apply_ms": n32_ms / max(n32_n, 1)}
+    # ---------------- the same step with compensated FP32 and with plain FP32 per-pixel accumulation
+    # (the plain one is outside the contract's precision: reported only for comparison)
+    for acc_alt, key, note in (("f32_kahan", "compensated_fp32_accumulation_step",
+                                "same step with compensated FP32 per-pixel sums (the contract's other precision)"),
+                               ("f32", "plain_fp32_accumulation_step",
+                                "same step with naive FP32 per-pixel sums (not the contract's precision)")):
+        with torch.cuda.stream(stream):
+            step(acc=acc_alt)
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nat.furax_profile_reset()
+            nat.furax_profile_enable(True)
+            e2.record(stream)
+            nsteps = max(1, min(args.steps, 3))
+            for _ in range(nsteps):
+                step(acc=acc_alt)
+            e3.record(stream)
+            stream.synchronize()
+            nat.furax_profile_enable(False)
+        alt_ms, alt_n = nat.furax_profile_read(0)
+        ms_alt = e2.elapsed_time(e3) / nsteps
+        out[key] = {"note": note, "ms_per_step": ms_alt, "value": samples_per_step / (ms_alt / 1e3) / 1e9,
+                    "unit": UNIT, "apply_ms": alt_ms / max(alt_n, 1)}
 
     # ---------------- per-unit rates of this GPU, configuration 1 in full, on-the-fly pointing
     if rank == 0 and not args.small:
         peaks = device_peaks(fx, dev, stream)
         out["device_peaks"] = peaks
+        # the headline kernel against the L2 reduction rate measured on this GPU: one FP64 reduction
+        # per Stokes component and sample (three per sample), the L2 operations it cannot avoid
+        if HEADLINE_ACC == "f64":
+            rate = 3.0 * S / (apply_ms / 1e3) / 1e9
+            pk = 3.0 * peaks["l2_random_red_3xf64_gops"]
+            out["l2_reduction_bound"] = {"bound": "l2_fp64_reductions", "achieved": rate, "peak": pk,
+                                         "unit": "G red.f64/s", "frac": rate / pk,
+                                         "note": "3 FP64 L2 reductions per sample; peak: furax_probe_l2 kind 3 "
+                                                 "(uniform random pixels of the nside-512 map)"}
         try:
             out["on_the_fly"] = on_the_fly_apply(fx, dev, stream, wl, q_bore, q_det, taps, peaks)
         except Exception as e:  # noqa: BLE001
