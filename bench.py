@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--l2-evict-first", type=int, default=0, choices=[0, 1])
     ap.add_argument("--consumer-warps", type=int, default=0, choices=[0, 8, 16])
     ap.add_argument("--no-tune", action="store_true", help="keep the default (time-ordered) schedule")
+    ap.add_argument("--no-alt", action="store_true",
+                    help="skip the steps with the other accumulations (profiling runs)")
     ap.add_argument("--tune-cache", default=None, help="JSON file of tuned schedules (default: the library's)")
     global ARGS
     ARGS = ap.parse_args()
@@ -987,7 +989,7 @@ def main():
 
     # ---------------- the same step with compensated FP32 and with plain FP32 per-pixel accumulation
     # (the plain one is outside the contract's precision: reported only for comparison)
-    for acc_alt, key, note in (("f32_kahan", "compensated_fp32_accumulation_step",
+    for acc_alt, key, note in () if args.no_alt else (("f32_kahan", "compensated_fp32_accumulation_step",
                                 "same step with compensated FP32 per-pixel sums (the contract's other precision)"),
                                ("f32", "plain_fp32_accumulation_step",
                                 "same step with naive FP32 per-pixel sums (not the contract's precision)")):
@@ -1009,7 +1011,7 @@ def main():
                     "unit": UNIT, "apply_ms": alt_ms / max(alt_n, 1)}
 
     # ---------------- per-unit rates of this GPU, configuration 1 in full, on-the-fly pointing
-    if rank == 0 and not args.small:
+    if rank == 0 and not args.small and not args.no_extra:
         peaks = device_peaks(fx, dev, stream)
         out["device_peaks"] = peaks
         # the headline kernel against the L2 reduction rate measured on this GPU: one FP64 reduction
