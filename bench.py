@@ -329,7 +329,8 @@ def device_peaks(fx, dev, stream):
         idx = torch.randint(0, ntab, (n,), generator=g, device=dev, dtype=torch.int32)
         table = torch.zeros(2 * ntab * 4, dtype=torch.float32, device=dev)   # 2 ntab float4 = 3 ntab doubles + room
         for name, kind in (("l2_random_gather_gops", 0), ("l2_random_red_v4_f32_gops", 1),
-                           ("l2_random_kahan_pair_gops", 2), ("l2_random_red_3xf64_gops", 3)):
+                           ("l2_random_kahan_pair_gops", 2), ("l2_random_red_3xf64_gops", 3),
+                           ("l2_random_red_3xf64_32B_records_gops", 4)):
             nat.furax_probe_l2(kind, idx, table, ntab, sink)
             e0.record(stream)
             nat.furax_probe_l2(kind, idx, table, ntab, sink)

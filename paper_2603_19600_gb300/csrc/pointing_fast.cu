@@ -82,7 +82,9 @@ __device__ __forceinline__ float frac_dist(float v)
 }
 
 // FP32 RING lookup with certified floors; false if any decision is within its error bound.
-__device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, int64_t nside, int32_t &pix)
+// Integer work is 32-bit (every index stays below 12 * 8192^2 < 2^31): conversions between FP32
+// and 64-bit integers would run on the FP64 pipe.
+__device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, int32_t nside, int32_t &pix)
 {
     const float rho2 = fmaf(dx, dx, dy * dy);
     if (!(rho2 >= 0.0025f)) return false;              // within ~3 deg of a pole (or NaN)
@@ -98,16 +100,16 @@ __device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, in
         const float a1 = t1 - t2, a2 = t1 + t2;
         const float m = 96.f * N * kU + 16.f * kU;
         if (frac_dist(a1) <= m || frac_dist(a2) <= m) return false;
-        const int64_t jp = (int64_t)floorf(a1), jm = (int64_t)floorf(a2);
-        const int64_t ir = nside + 1 + jp - jm;
-        const int64_t kshift = 1 - (ir & 1);
-        int64_t ip = (jp + jm - nside + kshift) / 2;
-        const int64_t nl4 = 4 * nside;
+        const int32_t jp = (int32_t)floorf(a1), jm = (int32_t)floorf(a2);
+        const int32_t ir = nside + 1 + jp - jm;
+        const int32_t kshift = 1 - (ir & 1);
+        int32_t ip = (jp + jm - nside + kshift) / 2;
+        const int32_t nl4 = 4 * nside;
         ip %= nl4;
         if (ip < 0) ip += nl4;
-        const int64_t p = 2 * nside * (nside - 1) + (ir - 1) * nl4 + ip;
+        const int32_t p = 2 * nside * (nside - 1) + (ir - 1) * nl4 + ip;
         if (p < 0 || p >= 12 * nside * nside) return false;
-        pix = (int32_t)p;
+        pix = p;
         return true;
     }
     const float ft = tt - floorf(tt);
@@ -116,17 +118,17 @@ __device__ __forceinline__ bool fast_ring_pixel(float dx, float dy, float dz, in
     const float b1 = ft * tmp, b2 = (1.f - ft) * tmp;
     const float mc = 112.f * N * kU + 16.f * kU;
     if (frac_dist(b1) <= mc || frac_dist(b2) <= mc) return false;
-    const int64_t jp = (int64_t)floorf(b1), jm = (int64_t)floorf(b2);
-    const int64_t ir = jp + jm + 1;
+    const int32_t jp = (int32_t)floorf(b1), jm = (int32_t)floorf(b2);
+    const int32_t ir = jp + jm + 1;
     const float b3 = tt * (float)ir;
     if (frac_dist(b3) <= 96.f * N * kU + 16.f * kU / rho + 64.f * kU) return false;
-    int64_t ip = (int64_t)floorf(b3);
-    const int64_t nl = 4 * ir;
+    int32_t ip = (int32_t)floorf(b3);
+    const int32_t nl = 4 * ir;
     ip %= nl;
     if (ip < 0) ip += nl;
-    const int64_t p = dz > 0.f ? 2 * ir * (ir - 1) + ip : 12 * nside * nside - 2 * ir * (ir + 1) + ip;
+    const int32_t p = dz > 0.f ? 2 * ir * (ir - 1) + ip : 12 * nside * nside - 2 * ir * (ir + 1) + ip;
     if (p < 0 || p >= 12 * nside * nside) return false;
-    pix = (int32_t)p;
+    pix = p;
     return true;
 }
 
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict
                         dz = dot3_df(mh + 6, ml + 6, dh, dl);
             const float ox = dot3_df(mh + 0, ml + 0, oh, ol), oy = dot3_df(mh + 3, ml + 3, oh, ol),
                         oz = dot3_df(mh + 6, ml + 6, oh, ol);
-            ok = fast_ring_pixel(dx, dy, dz, ob.nside, p);
+            ok = fast_ring_pixel(dx, dy, dz, (int32_t)ob.nside, p);
             if (ok) {
                 // psi from local north through east (same convention as the exact recipe)
                 const float rho2 = fmaf(dx, dx, dy * dy);

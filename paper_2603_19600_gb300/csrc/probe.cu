@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(PB) probe_fma_x2_kernel(int64_t iters, float b
 // Random L2 operations at the indices idx[0..n): kind 0 gathers a float4, 1 issues one
 // red.add.v4.f32, 2 the compensated pair (atom.add.v4.f32 returning the old value, red.add.v4.f32
 // of the rounding error into the second half of the table), 3 three red.add.f64 (one FP64 map
-// entry per Stokes component).
+// entry per Stokes component, [ntab][3] records), 4 the same into 32-byte records [ntab][4].
 __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *__restrict__ idx, int64_t n,
                                                       float4 *__restrict__ t4, double *__restrict__ t64, int64_t ntab,
                                                       float *__restrict__ sink)
@@ -84,9 +84,10 @@ __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *_
         } else if (kind == 2) {
             kahan_add_v4(t4 + p, t4 + ntab + p, v);
         } else {
-            red_add_f64(t64 + 3 * p, 1e-3);
-            red_add_f64(t64 + 3 * p + 1, 2e-3);
-            red_add_f64(t64 + 3 * p + 2, 3e-3);
+            const int64_t stride = kind == 3 ? 3 : 4;
+            red_add_f64(t64 + stride * p, 1e-3);
+            red_add_f64(t64 + stride * p + 1, 2e-3);
+            red_add_f64(t64 + stride * p + 2, 3e-3);
         }
     }
     if (acc == 12345.f) sink[0] = acc;
@@ -130,7 +131,7 @@ extern "C" furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink,
 extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable,
                                        void *sink, void *stream)
 {
-    if (kind < 0 || kind > 3) return set_error(FURAX_EINVAL, "kind must be in [0, 3]");
+    if (kind < 0 || kind > 4) return set_error(FURAX_EINVAL, "kind must be in [0, 4]");
     if (!idx || !table || !sink || n < 0 || ntable < 1) return set_error(FURAX_EINVAL, "invalid probe arguments");
     if (n == 0) return FURAX_OK;
     int dev = 0, sms = 1;
@@ -138,7 +139,7 @@ extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t
     if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     if (rc) return rc;
     // indices are the caller's: each must lie in [0, ntable) (float4 kinds: table holds 2 ntable
-    // float4 for kind 2; kind 3: 3 ntable doubles)
+    // float4 for kind 2; kind 3: 3 ntable doubles; kind 4: 4 ntable doubles)
     const unsigned g = (unsigned)std::min<int64_t>((n + PB - 1) / PB, 8LL * sms);
     probe_l2_kernel<<<g, PB, 0, (cudaStream_t)stream>>>(kind, idx, n, (float4 *)table, (double *)table, ntable,
                                                          (float *)sink);
