@@ -67,13 +67,23 @@ __global__ void __launch_bounds__(PB) probe_fma_x2_kernel(int64_t iters, float b
 // Random L2 operations at the indices idx[0..n): kind 0 gathers a float4, 1 issues one
 // red.add.v4.f32, 2 the compensated pair (atom.add.v4.f32 returning the old value, red.add.v4.f32
 // of the rounding error into the second half of the table), 3 three red.add.f64 (one FP64 map
-// entry per Stokes component, [ntab][3] records), 4 the same into 32-byte records [ntab][4].
+// entry per Stokes component, [ntab][3] records), 4 the same into 32-byte records [ntab][4],
+// 5 the same three reductions issued by three consecutive lanes of one instruction (lane 3k + c
+// adds component c of index k), so that one warp instruction covers a pixel's whole record.
 __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *__restrict__ idx, int64_t n,
                                                       float4 *__restrict__ t4, double *__restrict__ t64, int64_t ntab,
                                                       float *__restrict__ sink)
 {
     float acc = 0.f;
     const float4 v = make_float4(1e-3f, 2e-3f, 3e-3f, 0.f);
+    if (kind == 5) {
+        for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < 3 * n; f += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = f / 3;
+            const int c = (int)(f - 3 * i);
+            red_add_f64(t64 + 3 * (int64_t)idx[i] + c, 1e-3 * (c + 1));
+        }
+        return;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = idx[i];
         if (kind == 0) {
@@ -131,7 +141,7 @@ extern "C" furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink,
 extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable,
                                        void *sink, void *stream)
 {
-    if (kind < 0 || kind > 4) return set_error(FURAX_EINVAL, "kind must be in [0, 4]");
+    if (kind < 0 || kind > 5) return set_error(FURAX_EINVAL, "kind must be in [0, 5]");
     if (!idx || !table || !sink || n < 0 || ntable < 1) return set_error(FURAX_EINVAL, "invalid probe arguments");
     if (n == 0) return FURAX_OK;
     int dev = 0, sms = 1;
