@@ -12,10 +12,11 @@
 //   gather (7 warps): reads a landed stage, gathers the map values of the tile's pixels from
 //     the FP32 map in L2 (all loads of a thread issued before any is used) and writes the
 //     projected samples P x into one of kXsStages stages;
-//   consumer (8 warps): applies N^-1 (the 127-term symmetric band, 16 consecutive outputs per
+//   consumer (8 or 16 warps): applies N^-1 (the 127-term symmetric band, consecutive outputs per
 //     thread from a sliding register window), writes y over the consumed stage and scatters
-//     y (1, cos 2psi, sin 2psi) with one 16-byte L2 reduction per sample, lane-consecutive in
-//     time so that neighbouring samples of a warp share cache lines.
+//     y (1, cos 2psi, sin 2psi), lane-consecutive in time: one 16-byte FP32 L2 reduction per
+//     sample, the compensated pair of ACC_F32_KAHAN, or, for ACC_F64, three FP64 reductions per
+//     sample that the warp issues as whole 24-byte pixel records (red_add_f64x3_warp).
 // Shared memory is kept near 138 KB: the rest of the SM's L1/shared array is L1, where the
 // gathers' misses in flight are staged.
 // The pointing stream is read from HBM exactly once (plus 126 halo samples per tile); the map
@@ -338,6 +339,23 @@ __global__ void __launch_bounds__(tma_threads<KC>(), 1)
                         red_add_v4(acc_lo + kKahanStride * (ob.map_off + px[b]),
                                    kahan_error_v4(old[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f)));
             }
+        } else if constexpr (ACC == FURAX_ACC_F64) {
+            // three FP64 reductions per sample, issued as whole pixel records by the warp
+            double *base = acc64 + 3 * ob.map_off;
+#pragma unroll 4
+            for (int k = 0; k < kConsOut; ++k) {
+                const int u = tid + k * 32 * kTmaConsumer;
+                int32_t pix = u < tl.len ? S.pix[r][u + shift] : -1;
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+                if (pix >= 0) {
+                    float c = S.c[r][u + shift], s = S.s[r][u + shift];
+                    if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+                    v0 = ys[spos(u)];
+                    v1 = v0 * c;
+                    v2 = v0 * s;
+                }
+                red_add_f64x3_warp(base, pix, v0, v1, v2);
+            }
         } else {
 #pragma unroll 4
             for (int k = 0; k < kConsOut; ++k) {
@@ -348,14 +366,7 @@ __global__ void __launch_bounds__(tma_threads<KC>(), 1)
                 float c = S.c[r][u + shift], s = S.s[r][u + shift];
                 if (pv.psi_cs) rotate_psi<float>(c, s, cs);
                 const float yv = ys[spos(u)];
-                const int64_t gp = ob.map_off + pix;
-                const float4 v = make_float4(yv, yv * c, yv * s, 0.f);
-                if constexpr (ACC == FURAX_ACC_F32) red_add_v4(acc_hi + gp, v);
-                else {
-                    red_add_f64(acc64 + 3 * gp + 0, (double)v.x);
-                    red_add_f64(acc64 + 3 * gp + 1, (double)v.y);
-                    red_add_f64(acc64 + 3 * gp + 2, (double)v.z);
-                }
+                red_add_v4(acc_hi + ob.map_off + pix, make_float4(yv, yv * c, yv * s, 0.f));
             }
         }
         mbar_arrive(&S.xs_empty[q]);

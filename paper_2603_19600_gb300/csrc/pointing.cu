@@ -289,24 +289,22 @@ __global__ void __launch_bounds__(256) bj_accum_kernel(const Tile *__restrict__ 
                                                        const double *__restrict__ ninv_diag, double *__restrict__ m6,
                                                        int32_t *__restrict__ hits)
 {
+    // per-warp staging of the six block entries: the warp issues them as whole 48-byte records
+    __shared__ double stage[8][32 * 6];
+    __shared__ int32_t spix[8][32];
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = pv.obs[tl.obs];
     const double w0 = ninv_diag[ob.det_off + tl.det];
-    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-        const int64_t t = tl.t0 + k;
-        double c, s;
-        const int32_t pix = get_sample<MODE, double>(pv, ob, tl.det, t, c, s);
-        if (pix < 0) continue;
-        const int64_t gp = ob.map_off + pix;
-        double *m = m6 + 6 * gp;
+    const int warp = threadIdx.x >> 5;
+    double *base = m6 + 6 * ob.map_off;
+    for (int kw = threadIdx.x & ~31; kw < tl.len; kw += 256) {   // warp-uniform trip count
+        const int k = kw + (threadIdx.x & 31);
+        double c = 0.0, s = 0.0;
+        const int32_t pix = k < tl.len ? get_sample<MODE, double>(pv, ob, tl.det, tl.t0 + k, c, s) : -1;
         const double wc = w0 * c, ws = w0 * s;
-        red_add_f64(m + 0, w0);
-        red_add_f64(m + 1, wc);
-        red_add_f64(m + 2, ws);
-        red_add_f64(m + 3, wc * c);
-        red_add_f64(m + 4, wc * s);
-        red_add_f64(m + 5, ws * s);
-        red_add_s32(hits + gp, 1);
+        const double v[6] = {w0, wc, ws, wc * c, wc * s, ws * s};
+        red_add_f64_records_warp<6>(base, pix, v, stage[warp], spix[warp]);
+        if (pix >= 0) red_add_s32(hits + ob.map_off + pix, 1);
     }
 }
 
