@@ -3,8 +3,6 @@
 #pragma once
 #include <cstdint>
 
-#include "dfloat.cuh"
-
 namespace fx {
 
 __device__ __forceinline__ void red_add_f64(double *a, double v)
@@ -54,36 +52,18 @@ __device__ __forceinline__ float4 kahan_error_v4(float4 old, float4 v)
     return e;
 }
 
-// Warp-cooperative FP64 reductions into pixel records of three doubles, base[3 pix + c]: every lane
-// offers one sample (pix < 0: none) and its three values, and the warp's 96 reductions leave as three
-// instructions in which lane L of instruction i adds component (32 i + L) mod 3 of the sample of lane
-// (32 i + L) / 3. Consecutive lanes then address the consecutive doubles of one record, which the L2
-// serves together: 31 % more reductions per second on this GPU than one lane issuing a record's three
-// (furax_probe_l2 kinds 5 and 3). The samples reach their lanes by warp shuffles, FP32 values as
-// FP32, widened after the exchange (exactly, on the integer pipe). All 32 lanes of the warp call it,
-// with the same base.
-__device__ __forceinline__ void red_add_f64x3_warp(double *base, int32_t pix, float v0, float v1, float v2)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int f = 32 * i + lane;
-        const int src = f / 3, comp = f - 3 * src;
-        const int32_t p = __shfl_sync(0xffffffffu, pix, src);
-        const float w0 = __shfl_sync(0xffffffffu, v0, src);
-        const float w1 = __shfl_sync(0xffffffffu, v1, src);
-        const float w2 = __shfl_sync(0xffffffffu, v2, src);
-        const float w = comp == 0 ? w0 : (comp == 1 ? w1 : w2);
-        if (p >= 0) red_add_f64(base + 3 * (int64_t)p + comp, f32_to_f64_bits(w));
-    }
-}
-
-// The same for records of NC doubles and FP64 values, exchanged through a warp-private staging
-// area instead of shuffles (NC doubles per lane would take 2 NC shuffles per instruction):
-// buf holds 32 NC doubles and ibuf 32 ints, both owned by the calling warp.
-template <int NC>
-__device__ __forceinline__ void red_add_f64_records_warp(double *base, int32_t pix, const double (&v)[NC],
-                                                         double *buf, int32_t *ibuf)
+// Warp-cooperative FP64 reductions into pixel records of NC doubles, base[NC pix + c]: every lane
+// offers one sample (pix < 0: none) and its NC values, and the warp's 32 NC reductions leave as NC
+// instructions in which lane L of instruction i adds component (32 i + L) mod NC of the sample of
+// lane (32 i + L) / NC. Consecutive lanes then address the consecutive doubles of one record, which
+// the L2 serves together: for NC = 3, 31 % more reductions per second on this GPU than one lane
+// issuing a record's three (furax_probe_l2 kinds 5 and 3). The samples are exchanged through a
+// warp-private staging area (buf: 32 NC values, ibuf: 32 ints), which costs fewer instructions than
+// NC shuffles per instruction; FP32 values are widened to FP64 after the exchange. All 32 lanes of
+// the warp call it, with the same base.
+template <int NC, typename T>
+__device__ __forceinline__ void red_add_f64_records_warp(double *base, int32_t pix, const T (&v)[NC], T *buf,
+                                                         int32_t *ibuf)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -95,7 +75,7 @@ __device__ __forceinline__ void red_add_f64_records_warp(double *base, int32_t p
         const int f = 32 * i + lane;
         const int src = f / NC, comp = f - NC * src;
         const int32_t p = ibuf[src];
-        if (p >= 0) red_add_f64(base + (int64_t)NC * p + comp, buf[f]);
+        if (p >= 0) red_add_f64(base + (int64_t)NC * p + comp, (double)buf[f]);
     }
     __syncwarp();   // the staging area is free again
 }

@@ -433,38 +433,47 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
     }
     __syncthreads();
 
-    for (int k = threadIdx.x; k < tile.len; k += FT) {
-        float ch, cl, sh, sl;
-        const int32_t pix = sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl);
-        if (pix < 0) continue;
-        float yh = xs[spos(k)], ylo = yl[spos(k)];
-        if constexpr (TPL) {
-            const int64_t t = tile.t0 + k;
-            if (tpl_interior(tv, t, ob.nsamp)) {
-                const float j = (float)(k - (tile.len >> 1));
-                float vh = ecoef[3].x, vl = ecoef[3].y;
-                df_horner(vh, vl, j, ecoef[2].x, ecoef[2].y);
-                df_horner(vh, vl, j, ecoef[1].x, ecoef[1].y);
-                df_horner(vh, vl, j, ecoef[0].x, ecoef[0].y);
-                df_add(yh, ylo, -vh, -vl);
-            } else {
-                double w[4];
-                wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
-                double v = (double)yh + (double)ylo;
+    // Warp-uniform trip count: the FP64 head of each sample's contribution leaves through the
+    // warp's record-wise reductions (staging area below), which every lane joins; lanes past the
+    // tile or on masked samples offer pix = -1.
+    __shared__ float xv[FT / 32][96];
+    __shared__ int32_t xp[FT / 32][32];
+    double *rec = acc64 + 3 * ob.map_off;
+    for (int kw = threadIdx.x & ~31; kw < tile.len; kw += FT) {
+        const int k = kw + (threadIdx.x & 31);
+        float ch = 0.f, cl = 0.f, sh = 0.f, sl = 0.f;
+        const int32_t pix = k < tile.len ? sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl) : -1;
+        float yh = 0.f, qc = 0.f, qs = 0.f;
+        if (pix >= 0) {
+            yh = xs[spos(k)];
+            float ylo = yl[spos(k)];
+            if constexpr (TPL) {
+                const int64_t t = tile.t0 + k;
+                if (tpl_interior(tv, t, ob.nsamp)) {
+                    const float j = (float)(k - (tile.len >> 1));
+                    float vh = ecoef[3].x, vl = ecoef[3].y;
+                    df_horner(vh, vl, j, ecoef[2].x, ecoef[2].y);
+                    df_horner(vh, vl, j, ecoef[1].x, ecoef[1].y);
+                    df_horner(vh, vl, j, ecoef[0].x, ecoef[0].y);
+                    df_add(yh, ylo, -vh, -vl);
+                } else {
+                    double w[4];
+                    wt_eval<double>(nv, tv, gdet, ob.nsamp, t, w);
+                    double v = (double)yh + (double)ylo;
 #pragma unroll
-                for (int l = 0; l < 4; ++l) v -= tv.b[4 * gdet + l] * w[l];
-                split_df(v, yh, ylo);
+                    for (int l = 0; l < 4; ++l) v -= tv.b[4 * gdet + l] * w[l];
+                    split_df(v, yh, ylo);
+                }
             }
+            qc = __fmul_rn(yh, ch);
+            qs = __fmul_rn(yh, sh);
+            const float ec = __fmaf_rn(yh, ch, -qc), es = __fmaf_rn(yh, sh, -qs);
+            const float lc = __fadd_rn(ec, __fmaf_rn(ylo, ch, __fmul_rn(yh, cl)));
+            const float ls = __fadd_rn(es, __fmaf_rn(ylo, sh, __fmul_rn(yh, sl)));
+            red_add_v4(acc_lo + ob.map_off + pix, make_float4(ylo, lc, ls, 0.f));
         }
-        const float qc = __fmul_rn(yh, ch), qs = __fmul_rn(yh, sh);
-        const float ec = __fmaf_rn(yh, ch, -qc), es = __fmaf_rn(yh, sh, -qs);
-        const float lc = __fadd_rn(ec, __fmaf_rn(ylo, ch, __fmul_rn(yh, cl)));
-        const float ls = __fadd_rn(es, __fmaf_rn(ylo, sh, __fmul_rn(yh, sl)));
-        const int64_t gp = ob.map_off + pix;
-        red_add_f64(acc64 + 3 * gp + 0, f32_to_f64_bits(yh));
-        red_add_f64(acc64 + 3 * gp + 1, f32_to_f64_bits(qc));
-        red_add_f64(acc64 + 3 * gp + 2, f32_to_f64_bits(qs));
-        red_add_v4(acc_lo + gp, make_float4(ylo, lc, ls, 0.f));
+        const float v[3] = {yh, qc, qs};
+        red_add_f64_records_warp<3, float>(rec, pix, v, xv[threadIdx.x >> 5], xp[threadIdx.x >> 5]);
     }
 }
 

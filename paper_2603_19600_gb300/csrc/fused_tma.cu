@@ -16,7 +16,7 @@
 //     thread from a sliding register window), writes y over the consumed stage and scatters
 //     y (1, cos 2psi, sin 2psi), lane-consecutive in time: one 16-byte FP32 L2 reduction per
 //     sample, the compensated pair of ACC_F32_KAHAN, or, for ACC_F64, three FP64 reductions per
-//     sample that the warp issues as whole 24-byte pixel records (red_add_f64x3_warp).
+//     sample that the warp issues as whole 24-byte pixel records (red_add_f64_records_warp).
 // Shared memory is kept near 138 KB: the rest of the SM's L1/shared array is L1, where the
 // gathers' misses in flight are staged.
 // The pointing stream is read from HBM exactly once (plus 126 halo samples per tile); the map
@@ -54,10 +54,17 @@ struct TmaSmem {
     uint64_t raw_full[kRawStages], raw_empty[kRawStages], xs_full[kXsStages], xs_empty[kXsStages];
 };
 constexpr size_t kTmaSmem = sizeof(TmaSmem);
+// ACC_F64: behind the ring, one staging area per consumer warp for the record-wise FP64
+// reductions (96 values + 32 pixel indices).
+constexpr int kXchWords = 128;
+template <int ACC, int KC> constexpr size_t tma_smem()
+{
+    return kTmaSmem + (ACC == FURAX_ACC_F64 ? sizeof(float) * kXchWords * KC : 0);
+}
 // The SM's L1 cache and shared memory share one array, and global-load misses in flight are
 // staged in L1: the map gathers need at most ~150 KB of shared memory per SM to keep their
 // full rate (measured: a 206 KB reservation halves it).
-static_assert(kTmaSmem <= 150 * 1024, "leave L1 room for the gathers in flight");
+static_assert(tma_smem<FURAX_ACC_F64, 16>() <= 150 * 1024, "leave L1 room for the gathers in flight");
 static_assert(sizeof(int32_t) * kRawN % 16 == 0, "stage arrays stay 16-byte aligned");
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -340,21 +347,22 @@ __global__ void __launch_bounds__(tma_threads<KC>(), 1)
                                    kahan_error_v4(old[b], make_float4(v[b].x, v[b].y, v[b].z, 0.f)));
             }
         } else if constexpr (ACC == FURAX_ACC_F64) {
-            // three FP64 reductions per sample, issued as whole pixel records by the warp
+            // three FP64 reductions per sample, issued as whole pixel records by the warp through
+            // its staging area behind the ring (lanes past the tile offer pix = -1; the stage
+            // entries they read are in bounds and unused)
             double *base = acc64 + 3 * ob.map_off;
+            float *xv = reinterpret_cast<float *>(tsm + kTmaSmem) + (tid >> 5) * kXchWords;
+            int32_t *xp = reinterpret_cast<int32_t *>(xv + 96);
 #pragma unroll 4
             for (int k = 0; k < kConsOut; ++k) {
                 const int u = tid + k * 32 * kTmaConsumer;
-                int32_t pix = u < tl.len ? S.pix[r][u + shift] : -1;
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-                if (pix >= 0) {
-                    float c = S.c[r][u + shift], s = S.s[r][u + shift];
-                    if (pv.psi_cs) rotate_psi<float>(c, s, cs);
-                    v0 = ys[spos(u)];
-                    v1 = v0 * c;
-                    v2 = v0 * s;
-                }
-                red_add_f64x3_warp(base, pix, v0, v1, v2);
+                const bool in = u < tl.len;
+                const int32_t pix = in ? S.pix[r][u + shift] : -1;
+                float c = S.c[r][u + shift], s = S.s[r][u + shift];
+                if (pv.psi_cs) rotate_psi<float>(c, s, cs);
+                const float y0 = in ? ys[spos(u)] : 0.f;
+                const float v[3] = {y0, y0 * c, y0 * s};
+                red_add_f64_records_warp<3, float>(base, pix, v, xv, xp);
             }
         } else {
 #pragma unroll 4
@@ -379,7 +387,7 @@ static furax_status run_tma_kc(const furax_pointing *p, const furax_noise *n, co
                                float4 *lo, double *a64, const FusedTpl &ft, cudaStream_t st)
 {
     const unsigned g = (unsigned)std::min<int64_t>(p->n_tiles, p->n_sm);
-    return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL, KC>, g, tma_threads<KC>(), kTmaSmem, st, p->d_tiles,
+    return launch_dyn(fused_tma_kernel<ACC, BANDED, TPL, KC>, g, tma_threads<KC>(), tma_smem<ACC, KC>(), st, p->d_tiles,
                       p->n_tiles, p->view(), n->view(), x32, hi, lo, a64, p->d_err, ft, (int)p->sched.l2_evict_first);
 }
 
@@ -423,9 +431,9 @@ template <bool BANDED, int TPL, int KC>
 static furax_status prepare_tma_band()
 {
     furax_status rc = FURAX_OK;
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, BANDED, TPL, KC>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, BANDED, TPL, KC>, kTmaSmem);
-    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, BANDED, TPL, KC>, kTmaSmem);
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32, BANDED, TPL, KC>, tma_smem<FURAX_ACC_F32, KC>());
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F32_KAHAN, BANDED, TPL, KC>, tma_smem<FURAX_ACC_F32_KAHAN, KC>());
+    if (!rc) rc = allow_smem((const void *)fused_tma_kernel<FURAX_ACC_F64, BANDED, TPL, KC>, tma_smem<FURAX_ACC_F64, KC>());
     return rc;
 }
 

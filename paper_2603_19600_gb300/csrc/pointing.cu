@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) bj_accum_kernel(const Tile *__restrict__ 
         const int32_t pix = k < tl.len ? get_sample<MODE, double>(pv, ob, tl.det, tl.t0 + k, c, s) : -1;
         const double wc = w0 * c, ws = w0 * s;
         const double v[6] = {w0, wc, ws, wc * c, wc * s, ws * s};
-        red_add_f64_records_warp<6>(base, pix, v, stage[warp], spix[warp]);
+        red_add_f64_records_warp<6, double>(base, pix, v, stage[warp], spix[warp]);
         if (pix >= 0) red_add_s32(hits + ob.map_off + pix, 1);
     }
 }
