@@ -331,19 +331,26 @@ def device_peaks(fx, dev, stream):
         for name, kind in (("l2_random_gather_gops", 0), ("l2_random_red_v4_f32_gops", 1),
                            ("l2_random_kahan_pair_gops", 2), ("l2_random_red_3xf64_gops", 3),
                            ("l2_random_red_3xf64_32B_records_gops", 4),
-                           ("l2_random_red_3xf64_lane_interleaved_gops", 5)):
+                           ("l2_random_red_3xf64_lane_interleaved_gops", 5),
+                           ("l2_random_red_3xf64_lane_interleaved_batched_gops", 6),
+                           ("l2_random_gather_batched_gops", 7)):
             nat.furax_probe_l2(kind, idx, table, ntab, sink)
-            e0.record(stream)
-            nat.furax_probe_l2(kind, idx, table, ntab, sink)
-            e1.record(stream)
-            stream.synchronize()
-            out[name] = n / (e0.elapsed_time(e1) / 1e3) / 1e9
+            best = None
+            for _ in range(3):
+                e0.record(stream)
+                nat.furax_probe_l2(kind, idx, table, ntab, sink)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = n / (best / 1e3) / 1e9
         del idx, table
     out["how"] = ("FMA: 8 independent chains per thread, 8 x 256 threads per SM, best of 3 (2 flops per FMA); "
                   "L2: 2^26 uniform random indices into a 3,145,728-entry float4 table (50 MB, L2-resident), "
                   "one operation per index (the Kahan pair and the three FP64 reductions count as one; "
                   "'lane_interleaved': an index's three FP64 reductions issued by three consecutive lanes of one "
-                  "instruction, the issue pattern of the FP64 per-pixel sums)")
+                  "instruction, the issue pattern of the FP64 per-pixel sums; 'batched': 8 operations per thread "
+                  "in flight), best of 3 launches")
     return out
 
 
@@ -1066,13 +1073,15 @@ def main():
         # the rate of the issue pattern the kernel uses (a record's three by consecutive lanes)
         if HEADLINE_ACC == "f64":
             rate = 3.0 * S / (apply_ms / 1e3) / 1e9
-            pk = 3.0 * peaks["l2_random_red_3xf64_lane_interleaved_gops"]
+            pk = 3.0 * max(peaks["l2_random_red_3xf64_lane_interleaved_gops"],
+                           peaks["l2_random_red_3xf64_lane_interleaved_batched_gops"])
             out["l2_reduction_bound"] = {"bound": "l2_fp64_reductions", "achieved": rate, "peak": pk,
                                          "unit": "G red.f64/s", "frac": rate / pk,
-                                         "note": "3 FP64 L2 reductions per sample; peak: furax_probe_l2 kind 5 "
-                                                 "(a record's three reductions from consecutive lanes of one "
-                                                 "instruction, uniform random pixels of the nside-512 map); "
-                                                 "the same reductions from one lane each (kind 3) reach "
+                                         "note": "3 FP64 L2 reductions per sample; peak: the faster of "
+                                                 "furax_probe_l2 kinds 5 and 6 (a record's three reductions from "
+                                                 "consecutive lanes of one instruction, uniform random pixels of the "
+                                                 "nside-512 map; 6 with 8 per thread in flight); the same reductions "
+                                                 "from one lane each (kind 3) reach "
                                                  f"{3.0 * peaks['l2_random_red_3xf64_gops']:.1f} G/s"}
         try:
             out["on_the_fly"] = on_the_fly_apply(fx, dev, stream, wl, q_bore, q_det, taps, peaks)

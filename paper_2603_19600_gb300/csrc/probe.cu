@@ -69,13 +69,45 @@ __global__ void __launch_bounds__(PB) probe_fma_x2_kernel(int64_t iters, float b
 // of the rounding error into the second half of the table), 3 three red.add.f64 (one FP64 map
 // entry per Stokes component, [ntab][3] records), 4 the same into 32-byte records [ntab][4],
 // 5 the same three reductions issued by three consecutive lanes of one instruction (lane 3k + c
-// adds component c of index k), so that one warp instruction covers a pixel's whole record.
+// adds component c of index k), so that one warp instruction covers a pixel's whole record;
+// 6 kind 5 and 7 kind 0 with kProbeBatch operations per thread in flight (all index loads, then
+// all gathers or reductions), so that the L2, not the latency of a thread's index load, sets the
+// rate.
+constexpr int kProbeBatch = 8;
 __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *__restrict__ idx, int64_t n,
                                                       float4 *__restrict__ t4, double *__restrict__ t64, int64_t ntab,
                                                       float *__restrict__ sink)
 {
     float acc = 0.f;
     const float4 v = make_float4(1e-3f, 2e-3f, 3e-3f, 0.f);
+    if (kind == 6 || kind == 7) {
+        const int64_t total = kind == 6 ? 3 * n : n;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t f0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f0 < total; f0 += kProbeBatch * stride) {
+            int32_t p[kProbeBatch];
+#pragma unroll
+            for (int b = 0; b < kProbeBatch; ++b) {
+                const int64_t f = f0 + b * stride;
+                p[b] = f < total ? idx[kind == 6 ? f / 3 : f] : -1;
+            }
+            if (kind == 6) {
+#pragma unroll
+                for (int b = 0; b < kProbeBatch; ++b) {
+                    const int64_t f = f0 + b * stride;
+                    const int c = (int)(f % 3);
+                    if (p[b] >= 0) red_add_f64(t64 + 3 * (int64_t)p[b] + c, 1e-3 * (c + 1));
+                }
+            } else {
+                float4 m[kProbeBatch];
+#pragma unroll
+                for (int b = 0; b < kProbeBatch; ++b) m[b] = p[b] >= 0 ? __ldg(t4 + p[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < kProbeBatch; ++b) acc += m[b].x + m[b].y + m[b].z;
+            }
+        }
+        if (acc == 12345.f) sink[0] = acc;
+        return;
+    }
     if (kind == 5) {
         for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < 3 * n; f += (int64_t)gridDim.x * blockDim.x) {
             const int64_t i = f / 3;
@@ -141,7 +173,7 @@ extern "C" furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink,
 extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable,
                                        void *sink, void *stream)
 {
-    if (kind < 0 || kind > 5) return set_error(FURAX_EINVAL, "kind must be in [0, 5]");
+    if (kind < 0 || kind > 7) return set_error(FURAX_EINVAL, "kind must be in [0, 7]");
     if (!idx || !table || !sink || n < 0 || ntable < 1) return set_error(FURAX_EINVAL, "invalid probe arguments");
     if (n == 0) return FURAX_OK;
     int dev = 0, sms = 1;
@@ -149,7 +181,7 @@ extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t
     if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     if (rc) return rc;
     // indices are the caller's: each must lie in [0, ntable) (float4 kinds: table holds 2 ntable
-    // float4 for kind 2; kind 3: 3 ntable doubles; kind 4: 4 ntable doubles)
+    // float4 for kind 2; kinds 3, 5, 6: 3 ntable doubles; kind 4: 4 ntable doubles)
     const unsigned g = (unsigned)std::min<int64_t>((n + PB - 1) / PB, 8LL * sms);
     probe_l2_kernel<<<g, PB, 0, (cudaStream_t)stream>>>(kind, idx, n, (float4 *)table, (double *)table, ntable,
                                                          (float *)sink);
