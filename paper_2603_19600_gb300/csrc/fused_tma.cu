@@ -234,12 +234,15 @@ __global__ void __launch_bounds__(tma_threads<KC>(), 1)
                 const float4 amp = S.amp[r];
                 const float h = ob.nsamp > 1 ? 2.f / (float)(ob.nsamp - 1) : 0.f;
                 const float tau0 = ob.nsamp > 1 ? (float)t_first * h - 1.f : 0.f;
+                // (float)u without a conversion per sample: tid and the loop's strides convert
+                // exactly (integers below 2^24), so their FP32 sum is (float)u exactly
+                const float tidf = (float)tid;
 #pragma unroll 4
                 for (int k = 0; k < kGatherPer; ++k) {
                     const int u = tid + k * 32 * kTmaGather;
                     const int64_t t = t_first + u;
                     if (u < nload && t >= 0 && t < ob.nsamp) {
-                        const float tau = fmaf((float)u, h, tau0);
+                        const float tau = fmaf(tidf + (float)(k * 32 * kTmaGather), h, tau0);
                         S.xs[q][spos(u)] += fmaf(amp.z, 1.5f * tau * tau - 0.5f, fmaf(amp.y, tau, amp.x));
                     }
                 }
@@ -277,10 +280,13 @@ __global__ void __launch_bounds__(tma_threads<KC>(), 1)
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             if (base < tl.len) {
                 const float h = ob.nsamp > 1 ? 2.f / (float)(ob.nsamp - 1) : 0.f;
+                // one 64-bit conversion per thread instead of one per output (64-bit integer
+                // conversions run on the FP64 pipe); for t < 2^24 tb + i is (float)t exactly
+                const float tb = (float)(tl.t0 + base);
 #pragma unroll
                 for (int i = 0; i < kConsOut; ++i) {
                     if (base + i >= tl.len) break;
-                    const float tau = ob.nsamp > 1 ? (float)(tl.t0 + base + i) * h - 1.f : 0.f;
+                    const float tau = ob.nsamp > 1 ? (tb + (float)i) * h - 1.f : 0.f;
                     a[0] += y[i];
                     a[1] += tau * y[i];
                     a[2] += (1.5f * tau * tau - 0.5f) * y[i];
