@@ -435,8 +435,9 @@ def on_the_fly_apply(fx, dev, stream, wl, q_bore, q_det, taps, peaks, reps: int 
 
 def cg_to_1e8(fx, dev, stream, wl, q_bore, q_det, d):
     """Wall time to a true residual ||b - A64 x||/||b|| <= 1e-8 on the bench workload: mixed
-    precision (FP32 inner operator on a hi+lo pointing cache, double-FP32 right-hand side and
-    outer residual) vs plain FP64 PCG (FP64 cache, FP64 operator), same data, same system."""
+    precision (FP32 inner operator with FP64 per-pixel sums on a hi+lo pointing cache,
+    double-FP32 right-hand side and outer residual) vs plain FP64 PCG (FP64 cache, FP64
+    operator), same data, same system."""
     import torch
     nside, nd, ns = wl["nside"], wl["ndet"], wl["nsamp"]
     taps = np.tile(synth.inverse_noise_taps(), (nd, 1))
@@ -449,7 +450,7 @@ def cg_to_1e8(fx, dev, stream, wl, q_bore, q_det, d):
             for rep in range(2):   # the first run builds the CUDA graph and the workspaces
                 stream.synchronize()
                 t0 = time.perf_counter()
-                x, valid, inf = fx.mapmaker_cg(P, N, d, maxiter=2000, tol=1e-8, precision=prec, acc="f32_kahan",
+                x, valid, inf = fx.mapmaker_cg(P, N, d, maxiter=2000, tol=1e-8, precision=prec, acc=HEADLINE_ACC,
                                                inner_tol=1e-6, max_outer=20, rcond_min=1e-3)
                 stream.synchronize()
                 sec = time.perf_counter() - t0

@@ -314,6 +314,7 @@ static void pointing_free(furax_pointing *p)
     cudaFree(p->pix); cudaFree(p->c32); cudaFree(p->s32); cudaFree(p->c64); cudaFree(p->s64);
     cudaFree(p->c32lo); cudaFree(p->s32lo); cudaFree(p->ws_bore_m);
     cudaFree(p->ws_map32); cudaFree(p->ws_acc_hi); cudaFree(p->ws_acc64); cudaFree(p->ws_df_lo); cudaFree(p->ws_x64);
+    cudaFree(p->ws_x2);
     cudaFree(p->ws_tod); cudaFree(p->ws_tod2); cudaFree(p->ws_hits); cudaFree(p->d_err);
     delete p;
 }

@@ -283,15 +283,19 @@ __device__ __forceinline__ void dot2_step_x2(unsigned long long ch, unsigned lon
     E = f2_fma(cl, x, f2_add(E, f2_add(err, e)));
 }
 
-template <int R>
+// LO: the input is double-FP32 too (low words in xl), and each step adds the cross term
+// c_hi x_lo to the error word after c_lo x_hi, as dot2_step does.
+template <int R, bool LO = false>
 __device__ __forceinline__ void band_product_dfx2(const float *__restrict__ xs, const float4 *__restrict__ C4,
-                                                  const float2 *__restrict__ CL2, int base, float (&S)[R], float (&E)[R])
+                                                  const float2 *__restrict__ CL2, int base, float (&S)[R], float (&E)[R],
+                                                  const float *__restrict__ xl = nullptr)
 {
     constexpr int H = R / 2;
-    unsigned long long W[H], SS[H], EE[H];   // W[i] = (x[base+i+j], x[base+i+H+j]) at tap j
+    unsigned long long W[H], WL[LO ? H : 1], SS[H], EE[H];   // W[i] = (x[base+i+j], x[base+i+H+j]) at tap j
 #pragma unroll
     for (int i = 0; i < H; ++i) {
         W[i] = pack_f32x2(xs[spos(base + i)], xs[spos(base + i + H)]);
+        if constexpr (LO) WL[i] = pack_f32x2(xl[spos(base + i)], xl[spos(base + i + H)]);
         SS[i] = 0ull;
         EE[i] = 0ull;
     }
@@ -306,7 +310,10 @@ __device__ __forceinline__ void band_product_dfx2(const float *__restrict__ xs, 
                 const unsigned long long ch = pack_f32x2(c4.x, c4.y), nch = pack_f32x2(c4.z, c4.w);
                 const unsigned long long cl = pack_f32x2(c2.x, c2.y);
 #pragma unroll
-                for (int i = 0; i < H; ++i) dot2_step_x2(ch, nch, cl, W[i], SS[i], EE[i]);
+                for (int i = 0; i < H; ++i) {
+                    dot2_step_x2(ch, nch, cl, W[i], SS[i], EE[i]);
+                    if constexpr (LO) EE[i] = f2_fma(ch, WL[i], EE[i]);
+                }
                 if (j < kBand - 1) {
                     float lo0, hi0;
                     unpack_f32x2(W[0], lo0, hi0);
@@ -314,6 +321,13 @@ __device__ __forceinline__ void band_product_dfx2(const float *__restrict__ xs, 
 #pragma unroll
                     for (int i = 0; i < H - 1; ++i) W[i] = W[i + 1];
                     W[H - 1] = wl;
+                    if constexpr (LO) {
+                        unpack_f32x2(WL[0], lo0, hi0);
+                        const unsigned long long wll = pack_f32x2(hi0, xl[spos(base + R + j)]);
+#pragma unroll
+                        for (int i = 0; i < H - 1; ++i) WL[i] = WL[i + 1];
+                        WL[H - 1] = wll;
+                    }
                 }
             }
         }
@@ -477,6 +491,149 @@ __global__ void __launch_bounds__(FT, 2) df_rhs_kernel(const Tile *__restrict__ 
     }
 }
 
+// ------------------------------------------------------------------------------------
+// FP64-accurate normal operator on a map, acc64 + lo += P^T N^-1 P x, with no FP64 arithmetic
+// per sample (FP64 runs ~70x below FP32 on this GPU). x is split once per pixel into double-FP32
+// pairs; each sample's P x is formed in double-FP32 from those and the double-FP32 weights; N^-1
+// is the packed compensated band product with the input's low words; the scatter splits each
+// weighted term into an FP32 head, accumulated in FP64 as whole pixel records, and a tail,
+// accumulated in FP32 and folded in afterwards, as for the right-hand side.
+// ------------------------------------------------------------------------------------
+
+// x2[2 i] = high words (I, Q, U, 0) of x[i], x2[2 i + 1] = low words.
+__global__ void split_map_df_kernel(const double *__restrict__ x, float4 *__restrict__ x2, int64_t np)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        float h[3], l[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) split_df(x[3 * i + c], h[c], l[c]);
+        x2[2 * i] = make_float4(h[0], h[1], h[2], 0.f);
+        x2[2 * i + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
+// v = m0 + m1 c + m2 s in double-FP32 (m = mh + ml, c = ch + cl, s = sh + sl) as vh + vl: exact
+// products of the heads, two-sums of the head terms, and the remaining first-order terms in the
+// low word (the dropped ml cl, ml sl are ~2^-48 of the terms).
+__device__ __forceinline__ void df_weighted_sum(const float4 &mh, const float4 &ml, float ch, float cl, float sh,
+                                                float sl, float &vh, float &vl)
+{
+    const float p1 = __fmul_rn(mh.y, ch), e1 = __fmaf_rn(mh.y, ch, -p1);
+    const float p2 = __fmul_rn(mh.z, sh), e2 = __fmaf_rn(mh.z, sh, -p2);
+    const float s1 = __fadd_rn(mh.x, p1), t1 = two_sum_err(mh.x, p1, s1);
+    const float s2 = __fadd_rn(s1, p2), t2 = two_sum_err(s1, p2, s2);
+    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(t1, t2));
+    lo = __fmaf_rn(mh.y, cl, lo);
+    lo = __fmaf_rn(ml.y, ch, lo);
+    lo = __fmaf_rn(mh.z, sl, lo);
+    lo = __fmaf_rn(ml.z, sh, lo);
+    lo = __fadd_rn(lo, ml.x);
+    vh = __fadd_rn(s2, lo);
+    vl = two_sum_err(s2, lo, vh);
+}
+
+constexpr size_t kDfApplySmem = sizeof(float4) * kBandPad + sizeof(float2) * kBandPad + sizeof(float) * (2 * XS + 2 * MAXTAPS);
+
+template <int MODE, bool BANDED>
+__global__ void __launch_bounds__(FT, 2) df_apply_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+                                                         const float4 *__restrict__ x2, double *__restrict__ acc64,
+                                                         float4 *__restrict__ acc_lo)
+{
+    extern __shared__ __align__(16) float dsm_[];
+    float4 *C4 = reinterpret_cast<float4 *>(dsm_);           // [kBandPad] (c_hi, c_hi, -c_hi, -c_hi), tap order
+    float2 *CL2 = reinterpret_cast<float2 *>(C4 + kBandPad); // [kBandPad] (c_lo, c_lo)
+    float *xh = reinterpret_cast<float *>(CL2 + kBandPad);   // [XS] (P x)_hi over the tile and halos; then y_hi
+    float *xl = xh + XS;                                     // [XS] (P x)_lo; then y_lo
+    float *th = xl + XS;                                     // [MAXTAPS]
+    float *tl = th + MAXTAPS;                                // [MAXTAPS]
+    __shared__ float xv[FT / 32][96];
+    __shared__ int32_t xp[FT / 32][32];
+
+    const Tile tile = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tile.obs];
+    const int64_t gdet = ob.det_off + tile.det;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if (threadIdx.x < MAXTAPS) {
+        double c = 0.0;
+        if constexpr (BANDED) c = threadIdx.x < nv.ntaps ? nv.p64[gdet * nv.ntaps + threadIdx.x] : 0.0;
+        else c = threadIdx.x == 0 ? nv.p64[gdet] : 0.0;
+        split_df(c, th[threadIdx.x], tl[threadIdx.x]);
+    }
+    if (BANDED && threadIdx.x < kBandPad) {
+        const int j = threadIdx.x, k = j < kHalo ? kHalo - j : j - kHalo;
+        float h = 0.f, l = 0.f;
+        if (j < kBand && k < nv.ntaps) split_df(nv.p64[gdet * nv.ntaps + k], h, l);
+        C4[j] = make_float4(h, h, -h, -h);
+        CL2[j] = make_float2(l, l);
+    }
+    const int nload = tile.len + 2 * halo;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tile.t0 - halo + u;
+        float vh = 0.f, vl = 0.f;
+        if (t >= 0 && t < ob.nsamp) {
+            float ch, cl, sh, sl;
+            const int32_t pix = sample_df<MODE>(pv, ob, tile.det, t, ch, cl, sh, sl);
+            if (pix >= 0) {
+                const int64_t gp = ob.map_off + pix;
+                df_weighted_sum(x2[2 * gp], x2[2 * gp + 1], ch, cl, sh, sl, vh, vl);
+            }
+        }
+        xh[spos(u)] = vh;
+        xl[spos(u)] = vl;
+    }
+    __syncthreads();
+
+    const int base = threadIdx.x * FR;
+    float S[FR], E[FR];
+    if (base < tile.len) {
+        if constexpr (BANDED) {
+            band_product_dfx2<FR, true>(xh, C4, CL2, base, S, E, xl);
+        } else {
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                S[r] = 0.f;
+                E[r] = 0.f;
+                dot2_step(th[0], tl[0], xh[spos(base + r)], xl[spos(base + r)], S[r], E[r]);
+            }
+        }
+    }
+    __syncthreads();   // every stencil input has been read: y overwrites the tile in place
+    if (base < tile.len) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            if (base + r < tile.len) {
+                const float h = __fadd_rn(S[r], E[r]);          // |S| >= |E|: fast two-sum
+                xh[spos(base + r)] = h;
+                xl[spos(base + r)] = __fsub_rn(E[r], __fsub_rn(h, S[r]));
+            }
+        }
+    }
+    __syncthreads();
+
+    // Warp-uniform trip count for the warp's record-wise reductions (lanes past the tile or on
+    // masked samples offer pix = -1); the weights are read again (the tile's stretch of the
+    // pointing stream is in L2 from the gather above).
+    double *rec = acc64 + 3 * ob.map_off;
+    for (int kw = threadIdx.x & ~31; kw < tile.len; kw += FT) {
+        const int k = kw + (threadIdx.x & 31);
+        float ch = 0.f, cl = 0.f, sh = 0.f, sl = 0.f;
+        const int32_t pix = k < tile.len ? sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl) : -1;
+        float yh = 0.f, qc = 0.f, qs = 0.f;
+        if (pix >= 0) {
+            yh = xh[spos(k)];
+            const float ylo = xl[spos(k)];
+            qc = __fmul_rn(yh, ch);
+            qs = __fmul_rn(yh, sh);
+            const float ec = __fmaf_rn(yh, ch, -qc), es = __fmaf_rn(yh, sh, -qs);
+            const float lc = __fadd_rn(ec, __fmaf_rn(ylo, ch, __fmul_rn(yh, cl)));
+            const float ls = __fadd_rn(es, __fmaf_rn(ylo, sh, __fmul_rn(yh, sl)));
+            red_add_v4(acc_lo + ob.map_off + pix, make_float4(ylo, lc, ls, 0.f));
+        }
+        const float v[3] = {yh, qc, qs};
+        red_add_f64_records_warp<3, float>(rec, pix, v, xv[threadIdx.x >> 5], xp[threadIdx.x >> 5]);
+    }
+}
+
 // acc64 += lo (per pixel, then lo is no longer needed).
 __global__ void fold_lo_kernel(const float4 *__restrict__ lo, double *__restrict__ acc64, int64_t np)
 {
@@ -529,6 +686,50 @@ static furax_status launch_df_rhs_f32(const furax_pointing *p, const furax_noise
     return check_launch("fold low words");
 }
 
+template <int MODE, bool B>
+static furax_status run_df_apply(const furax_pointing *p, const furax_noise *n, const float4 *x2, double *a64,
+                                 float4 *lo, cudaStream_t st)
+{
+    return launch_dyn(df_apply_kernel<MODE, B>, (unsigned)p->n_tiles, FT, kDfApplySmem, st, p->d_tiles, p->view(),
+                      n->view(), x2, a64, lo);
+}
+
+// acc64 += P^T N^-1 P x on the FP32 units: split x, apply, fold the low words.
+static furax_status launch_df_apply(const furax_pointing *p, const furax_noise *n, const double *x, double *a64,
+                                    cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    furax_status rc;
+    const int64_t np = p->npix_total;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_x2, sizeof(float4) * 2 * np))) return rc;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_df_lo, sizeof(float4) * np))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(pm->ws_df_lo, 0, sizeof(float4) * np, st), "memset"))) return rc;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, (int64_t)p->n_sm * 8));
+    split_map_df_kernel<<<g, 256, 0, st>>>(x, pm->ws_x2, np);
+    count_launches(1);
+    if ((rc = check_launch("double-FP32 split of the map"))) return rc;
+    const bool b = n->kind == FURAX_NOISE_BANDED;
+    switch (p->mode) {
+    case FURAX_POINTING_ON_THE_FLY:
+        rc = b ? run_df_apply<0, true>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st) : run_df_apply<0, false>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st);
+        break;
+    case FURAX_POINTING_CACHE_F32:
+        rc = b ? run_df_apply<1, true>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st) : run_df_apply<1, false>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st);
+        break;
+    case FURAX_POINTING_CACHE_MIXED:
+        rc = b ? run_df_apply<3, true>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st) : run_df_apply<3, false>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st);
+        break;
+    default:
+        rc = b ? run_df_apply<2, true>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st) : run_df_apply<2, false>(p, n, pm->ws_x2, a64, pm->ws_df_lo, st);
+    }
+    if (rc) return rc;
+    count_launches(1);
+    if ((rc = check_launch("double-FP32 P^T N^-1 P"))) return rc;
+    fold_lo_kernel<<<g, 256, 0, st>>>(pm->ws_df_lo, a64, np);
+    count_launches(1);
+    return check_launch("fold low words");
+}
+
 template <int MODE, bool BANDED, bool FROM_TOD, typename DT>
 static furax_status run_df(const furax_pointing *p, const furax_noise *n, const double *x, const DT *d, double *a64,
                            cudaStream_t st)
@@ -565,8 +766,8 @@ furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, cons
         const TplView tv = tp ? tp->view() : TplView{};
         return launch_df_rhs_f32(p, n, (const float *)d, acc64, st, tp ? &tv : nullptr);
     }
-    if (!d) rc = dispatch_df<false, double>(p, n, x, (const double *)nullptr, acc64, st);
-    else if (d_t == FURAX_F64) rc = dispatch_df<true, double>(p, n, nullptr, (const double *)d, acc64, st);
+    if (!d) return launch_df_apply(p, n, x, acc64, st);
+    if (d_t == FURAX_F64) rc = dispatch_df<true, double>(p, n, nullptr, (const double *)d, acc64, st);
     else rc = dispatch_df<true, float>(p, n, nullptr, (const float *)d, acc64, st);
     if (rc) return rc;
     count_launches(1);
@@ -577,11 +778,11 @@ template <int MODE, bool B>
 static furax_status prep_df_mode_band()
 {
     furax_status rc = FURAX_OK;
-    if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, false, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, double>, kDfSmem);
     if (!rc) rc = allow_smem((const void *)fused_df_kernel<MODE, B, true, float>, kDfSmem);
     if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, false>, kDfRhsSmem);
     if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, true>, kDfRhsSmem);
+    if (!rc && kDfApplySmem > 48 * 1024) rc = allow_smem((const void *)df_apply_kernel<MODE, B>, kDfApplySmem);
     return rc;
 }
 

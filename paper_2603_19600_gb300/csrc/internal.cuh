@@ -179,7 +179,8 @@ struct furax_pointing {
     float4 *ws_acc_hi = nullptr;      // [2 npix] FP32 accumulator (I,Q,U,-): plain hi[i], or compensated
                                       // hi[2i] with its compensation at hi[2i + 1] (atomics.cuh)
     double *ws_acc64 = nullptr;       // [npix][3] FP64 accumulator
-    float4 *ws_df_lo = nullptr;       // [npix] FP32 low-word accumulator of the double-FP32 RHS
+    float4 *ws_df_lo = nullptr;       // [npix] FP32 low-word accumulator of the double-FP32 RHS and operator
+    float4 *ws_x2 = nullptr;          // [npix][2] double-FP32 split (high, low words) of an FP64 map
     double *ws_x64 = nullptr;         // [npix][3] masked FP64 copy
     void *ws_tod = nullptr;           // [nsamp] scratch TOD (FP64 size)
     void *ws_tod2 = nullptr;
