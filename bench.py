@@ -775,7 +775,7 @@ def gradient_c5(fx, dev, stream, reps: int = 3):
         sky = torch.from_numpy(synth.gaussian_sky(nside, g)).to(dev)
         d = P.apply(sky)
         m = sky * 1.01
-        for prec, dd in (("f64", d), ("f32", d.float())):
+        for prec, dd in (("f64", d), ("f32x2", d), ("f32", d.float())):
             fx.chi2_grad(P, N, dd, m, prec)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             stream.synchronize()

@@ -426,7 +426,10 @@ furax_status furax_gapfill(const furax_noise_t *cov, const void *d, const uint8_
  * grad_psi[j] = -2 sum_t (N^-1 r)_{j,t} * 2 (U_p cos 2psi - Q_p sin 2psi) (offsets included).
  * d device [nsamp_total] of d_t; m device FP64 [npix_total][3]; chi2 device FP64 [n_obs]
  * (per observation); grad_map device FP64 [npix_total][3] or NULL; grad_psi device FP64
- * [sum ndet] or NULL. precision FURAX_F32: residual and N^-1 in FP32, sums in FP64. */
+ * [sum ndet] or NULL. precision FURAX_F64: everything in FP64; FURAX_F32: residual, N^-1 and
+ * each thread's partial sums in FP32, sums across threads and the map gradient in FP64;
+ * FURAX_PREC_F32X2: FP64-accurate in double-FP32 on the FP32 units (residual, compensated band
+ * product, partial sums), sums across threads and the map gradient in FP64. */
 furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, const void *d, int32_t d_t,
                              const double *m, double *chi2, double *grad_map, double *grad_psi,
                              int32_t precision, void *stream);

@@ -820,7 +820,7 @@ furax_status furax_chi2_grad(const furax_pointing_t *p, const furax_noise_t *n, 
     furax_status rc = check_pair(p, n);
     if (rc) return rc;
     REQUIRE(d && m && chi2, "d, m and chi2 must be device pointers");
-    REQUIRE(valid_dtype(d_t) && valid_dtype(precision), "unknown dtype");
+    REQUIRE(valid_dtype(d_t) && (valid_dtype(precision) || precision == FURAX_PREC_F32X2), "unknown dtype or precision");
     REQUIRE(!long_band(n), "chi2 and its gradients take bands of at most %d taps", MAXTAPS);
     return launch_chi2_grad(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, (cudaStream_t)stream);
 }

@@ -634,6 +634,181 @@ __global__ void __launch_bounds__(FT, 2) df_apply_kernel(const Tile *__restrict_
     }
 }
 
+// ------------------------------------------------------------------------------------
+// chi^2 = r^T N^-1 r, r = d - P m, with grad_map = -2 P^T N^-1 r and
+// grad_psi = -2 sum (N^-1 r) 2 (U c - Q s), FP64-accurate on the FP32 units (precision
+// FURAX_PREC_F32X2): r in double-FP32 from the split map and double-FP32 weights, N^-1 r by the
+// packed compensated band product, each thread's sums as double-FP32 pairs (FP64 across threads),
+// and the map gradient as FP32 heads reduced in FP64 records plus FP32 tails folded afterwards.
+// ------------------------------------------------------------------------------------
+
+// (ah, al) += (xh + xl)(yh + yl), the product's head exact by FMA, its tail and the cross terms
+// in the low word.
+__device__ __forceinline__ void df_mac(float xh, float xl, float yh, float yl, float &ah, float &al)
+{
+    const float p = __fmul_rn(xh, yh), e = __fmaf_rn(xh, yh, -p);
+    const float s = __fadd_rn(ah, p), t = two_sum_err(ah, p, s);
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(t, __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, e))));
+}
+
+template <typename DT>
+__device__ __forceinline__ void data_df(DT v, float &h, float &l)
+{
+    if constexpr (sizeof(DT) == 8) {
+        h = f64_to_f32_bits(v);
+        l = f64_to_f32_bits(v - f32_to_f64_bits(h));   // exact difference, one FP64 subtraction
+    } else {
+        h = v;
+        l = 0.f;
+    }
+}
+
+template <int MODE, bool BANDED, typename DT>
+__global__ void __launch_bounds__(FT, 2) chi2_df_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
+                                                        const DT *__restrict__ d, const float4 *__restrict__ m2,
+                                                        double *__restrict__ chi2, double *__restrict__ grad_map,
+                                                        float4 *__restrict__ gm_lo, double *__restrict__ grad_psi)
+{
+    extern __shared__ __align__(16) float csm_[];
+    float4 *C4 = reinterpret_cast<float4 *>(csm_);           // [kBandPad] (c_hi, c_hi, -c_hi, -c_hi), tap order
+    float2 *CL2 = reinterpret_cast<float2 *>(C4 + kBandPad); // [kBandPad] (c_lo, c_lo)
+    float *xh = reinterpret_cast<float *>(CL2 + kBandPad);   // [XS] r_hi over the tile and halos; then y_hi
+    float *xl = xh + XS;                                     // [XS] r_lo; then y_lo
+    float *th = xl + XS;                                     // [MAXTAPS]
+    float *tl = th + MAXTAPS;                                // [MAXTAPS]
+    __shared__ float xv[FT / 32][96];
+    __shared__ int32_t xp[FT / 32][32];
+    __shared__ double red[2][FT / 32];
+
+    const Tile tile = tiles[blockIdx.x];
+    const ObsInfo ob = pv.obs[tile.obs];
+    const int64_t gdet = ob.det_off + tile.det;
+    const int64_t row = ob.tod_off + tile.det * ob.nsamp;
+    constexpr int halo = BANDED ? kHalo : 0;
+    if (threadIdx.x < MAXTAPS) {
+        double c = 0.0;
+        if constexpr (BANDED) c = threadIdx.x < nv.ntaps ? nv.p64[gdet * nv.ntaps + threadIdx.x] : 0.0;
+        else c = threadIdx.x == 0 ? nv.p64[gdet] : 0.0;
+        split_df(c, th[threadIdx.x], tl[threadIdx.x]);
+    }
+    if (BANDED && threadIdx.x < kBandPad) {
+        const int j = threadIdx.x, k = j < kHalo ? kHalo - j : j - kHalo;
+        float h = 0.f, l = 0.f;
+        if (j < kBand && k < nv.ntaps) split_df(nv.p64[gdet * nv.ntaps + k], h, l);
+        C4[j] = make_float4(h, h, -h, -h);
+        CL2[j] = make_float2(l, l);
+    }
+    const int nload = tile.len + 2 * halo;
+    for (int u = threadIdx.x; u < nload; u += FT) {
+        const int64_t t = tile.t0 - halo + u;
+        float rh = 0.f, rl = 0.f;
+        if (t >= 0 && t < ob.nsamp) {
+            float ch, cl, sh, sl, vh = 0.f, vl = 0.f, dh, dl;
+            const int32_t pix = sample_df<MODE>(pv, ob, tile.det, t, ch, cl, sh, sl);
+            if (pix >= 0) {
+                const int64_t gp = ob.map_off + pix;
+                df_weighted_sum(m2[2 * gp], m2[2 * gp + 1], ch, cl, sh, sl, vh, vl);
+            }
+            data_df(d[row + t], dh, dl);
+            // r = d - model: two-sum of the heads, the low words in the tail
+            const float sdiff = __fsub_rn(dh, vh), e = two_sum_err(dh, -vh, sdiff);
+            const float lo = __fadd_rn(e, __fsub_rn(dl, vl));
+            rh = __fadd_rn(sdiff, lo);
+            rl = two_sum_err(sdiff, lo, rh);
+        }
+        xh[spos(u)] = rh;
+        xl[spos(u)] = rl;
+    }
+    __syncthreads();
+
+    const int base = threadIdx.x * FR;
+    float S[FR], E[FR];
+    float ah = 0.f, al = 0.f;   // this thread's part of r^T N^-1 r
+    if (base < tile.len) {
+        if constexpr (BANDED) {
+            band_product_dfx2<FR, true>(xh, C4, CL2, base, S, E, xl);
+        } else {
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                S[r] = 0.f;
+                E[r] = 0.f;
+                dot2_step(th[0], tl[0], xh[spos(base + r)], xl[spos(base + r)], S[r], E[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            if (base + r >= tile.len) break;
+            const float h = __fadd_rn(S[r], E[r]);              // |S| >= |E|: fast two-sum
+            const float l = __fsub_rn(E[r], __fsub_rn(h, S[r]));
+            S[r] = h;
+            E[r] = l;
+            df_mac(xh[spos(base + r + halo)], xl[spos(base + r + halo)], h, l, ah, al);
+        }
+    }
+    __syncthreads();   // every stencil input has been read: y overwrites the tile in place
+    if (base < tile.len) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            if (base + r < tile.len) {
+                xh[spos(base + r)] = S[r];
+                xl[spos(base + r)] = E[r];
+            }
+        }
+    }
+    __syncthreads();
+
+    float bh = 0.f, bl = 0.f;   // this thread's part of sum y (U c - Q s)
+    double *rec = grad_map ? grad_map + 3 * ob.map_off : nullptr;
+    for (int kw = threadIdx.x & ~31; kw < tile.len; kw += FT) {   // warp-uniform trip count
+        const int k = kw + (threadIdx.x & 31);
+        float ch = 0.f, cl = 0.f, sh = 0.f, sl = 0.f;
+        const int32_t pix = k < tile.len ? sample_df<MODE>(pv, ob, tile.det, tile.t0 + k, ch, cl, sh, sl) : -1;
+        float gh = 0.f, qc = 0.f, qs = 0.f;
+        if (pix >= 0) {
+            const float yh = xh[spos(k)], yl = xl[spos(k)];
+            const int64_t gp = ob.map_off + pix;
+            const float4 mh = m2[2 * gp], ml = m2[2 * gp + 1];
+            // w = U c - Q s in double-FP32, then (bh, bl) += y w
+            float uh = 0.f, ul = 0.f;
+            df_mac(mh.z, ml.z, ch, cl, uh, ul);
+            df_mac(-mh.y, -ml.y, sh, sl, uh, ul);
+            const float wh = __fadd_rn(uh, ul), wl = two_sum_err(uh, ul, wh);
+            df_mac(yh, yl, wh, wl, bh, bl);
+            if (rec) {
+                gh = -2.f * yh;   // exact
+                const float gl = -2.f * yl;
+                qc = __fmul_rn(gh, ch);
+                qs = __fmul_rn(gh, sh);
+                const float ec = __fmaf_rn(gh, ch, -qc), es = __fmaf_rn(gh, sh, -qs);
+                const float lc = __fadd_rn(ec, __fmaf_rn(gl, ch, __fmul_rn(gh, cl)));
+                const float ls = __fadd_rn(es, __fmaf_rn(gl, sh, __fmul_rn(gh, sl)));
+                red_add_v4(gm_lo + gp, make_float4(gl, lc, ls, 0.f));
+            }
+        }
+        if (rec) {
+            const float v[3] = {gh, qc, qs};
+            red_add_f64_records_warp<3, float>(rec, pix, v, xv[threadIdx.x >> 5], xp[threadIdx.x >> 5]);
+        }
+    }
+    // block reduction (fixed order within the block), in FP64 across threads
+    double a = (double)ah + (double)al;
+    double b = (ob.hwp ? -2.0 : 2.0) * ((double)bh + (double)bl);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = a; red[1][threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < FT / 32; ++w) { sa += red[0][w]; sb += red[1][w]; }
+        red_add_f64(chi2 + tile.obs, sa);
+        if (grad_psi) red_add_f64(grad_psi + gdet, -2.0 * sb);
+    }
+}
+
 // acc64 += lo (per pixel, then lo is no longer needed).
 __global__ void fold_lo_kernel(const float4 *__restrict__ lo, double *__restrict__ acc64, int64_t np)
 {
@@ -730,6 +905,56 @@ static furax_status launch_df_apply(const furax_pointing *p, const furax_noise *
     return check_launch("fold low words");
 }
 
+template <int MODE, typename DT>
+static furax_status run_chi2_df(const furax_pointing *p, const furax_noise *n, const DT *d, const float4 *m2,
+                                double *chi2, double *gm, float4 *lo, double *gp, cudaStream_t st)
+{
+    if (n->kind == FURAX_NOISE_BANDED)
+        return launch_dyn(chi2_df_kernel<MODE, true, DT>, (unsigned)p->n_tiles, FT, kDfApplySmem, st, p->d_tiles,
+                          p->view(), n->view(), d, m2, chi2, gm, lo, gp);
+    return launch_dyn(chi2_df_kernel<MODE, false, DT>, (unsigned)p->n_tiles, FT, kDfApplySmem, st, p->d_tiles,
+                      p->view(), n->view(), d, m2, chi2, gm, lo, gp);
+}
+
+template <typename DT>
+static furax_status dispatch_chi2_df(const furax_pointing *p, const furax_noise *n, const DT *d, const float4 *m2,
+                                     double *chi2, double *gm, float4 *lo, double *gp, cudaStream_t st)
+{
+    switch (p->mode) {
+    case FURAX_POINTING_ON_THE_FLY: return run_chi2_df<0, DT>(p, n, d, m2, chi2, gm, lo, gp, st);
+    case FURAX_POINTING_CACHE_F32: return run_chi2_df<1, DT>(p, n, d, m2, chi2, gm, lo, gp, st);
+    case FURAX_POINTING_CACHE_MIXED: return run_chi2_df<3, DT>(p, n, d, m2, chi2, gm, lo, gp, st);
+    default: return run_chi2_df<2, DT>(p, n, d, m2, chi2, gm, lo, gp, st);
+    }
+}
+
+// chi^2 and gradients in double-FP32 (the outputs are cleared by the caller): split m, run,
+// fold the map gradient's low words.
+furax_status launch_chi2_df(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, const double *m,
+                            double *chi2, double *grad_map, double *grad_psi, cudaStream_t st)
+{
+    furax_pointing *pm = const_cast<furax_pointing *>(p);
+    furax_status rc;
+    const int64_t np = p->npix_total;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_x2, sizeof(float4) * 2 * np))) return rc;
+    if ((rc = ensure_ws(pm, (void **)&pm->ws_df_lo, sizeof(float4) * np))) return rc;
+    if (grad_map && (rc = check_cuda(cudaMemsetAsync(pm->ws_df_lo, 0, sizeof(float4) * np, st), "memset"))) return rc;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, (int64_t)p->n_sm * 8));
+    split_map_df_kernel<<<g, 256, 0, st>>>(m, pm->ws_x2, np);
+    count_launches(1);
+    if ((rc = check_launch("double-FP32 split of the map"))) return rc;
+    rc = d_t == FURAX_F64
+             ? dispatch_chi2_df<double>(p, n, (const double *)d, pm->ws_x2, chi2, grad_map, pm->ws_df_lo, grad_psi, st)
+             : dispatch_chi2_df<float>(p, n, (const float *)d, pm->ws_x2, chi2, grad_map, pm->ws_df_lo, grad_psi, st);
+    if (rc) return rc;
+    count_launches(1);
+    if ((rc = check_launch("double-FP32 chi2 and gradients"))) return rc;
+    if (!grad_map) return FURAX_OK;
+    fold_lo_kernel<<<g, 256, 0, st>>>(pm->ws_df_lo, grad_map, np);
+    count_launches(1);
+    return check_launch("fold low words");
+}
+
 template <int MODE, bool BANDED, bool FROM_TOD, typename DT>
 static furax_status run_df(const furax_pointing *p, const furax_noise *n, const double *x, const DT *d, double *a64,
                            cudaStream_t st)
@@ -783,6 +1008,8 @@ static furax_status prep_df_mode_band()
     if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, false>, kDfRhsSmem);
     if (!rc && kDfRhsSmem > 48 * 1024) rc = allow_smem((const void *)df_rhs_kernel<MODE, B, true>, kDfRhsSmem);
     if (!rc && kDfApplySmem > 48 * 1024) rc = allow_smem((const void *)df_apply_kernel<MODE, B>, kDfApplySmem);
+    if (!rc && kDfApplySmem > 48 * 1024) rc = allow_smem((const void *)chi2_df_kernel<MODE, B, double>, kDfApplySmem);
+    if (!rc && kDfApplySmem > 48 * 1024) rc = allow_smem((const void *)chi2_df_kernel<MODE, B, float>, kDfApplySmem);
     return rc;
 }
 

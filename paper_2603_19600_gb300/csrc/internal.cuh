@@ -324,6 +324,8 @@ furax_status launch_fused_f64(const furax_pointing *p, const furax_noise *n, con
 // acc64 += P^T N^-1 d when d != nullptr.
 // tp (FP32 d only): fold the template correction -P^T (W T) b of the deprojected right-hand side into
 // the same pass, with b already solved by launch_tpl_rhs_amplitudes.
+furax_status launch_chi2_df(const furax_pointing *p, const furax_noise *n, const void *d, int d_t, const double *m,
+                            double *chi2, double *grad_map, double *grad_psi, cudaStream_t st);
 furax_status launch_fused_df(const furax_pointing *p, const furax_noise *n, const double *x, const void *d, int d_t,
                              double *acc64, cudaStream_t st, const furax_templates *tp = nullptr);
 // b = P^T N^-1 d accumulated into acc64 (FP64 stencil)

@@ -343,6 +343,7 @@ furax_status launch_chi2_grad(const furax_pointing *p, const furax_noise *n, con
     if (grad_psi && (rc = check_cuda(cudaMemsetAsync(grad_psi, 0, sizeof(double) * p->ndet_total, st), "memset")))
         return rc;
     if (p->n_tiles == 0) return FURAX_OK;
+    if (precision == FURAX_PREC_F32X2) return launch_chi2_df(p, n, d, d_t, m, chi2, grad_map, grad_psi, st);
     if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_chi2<0>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);
     else if (p->mode == FURAX_POINTING_CACHE_F32)
         rc = dispatch_chi2<1>(p, n, d, d_t, m, chi2, grad_map, grad_psi, precision, st);

@@ -28,7 +28,7 @@ def _oracle(orc, o, taps, delta, m, d):
     return orc.chi2_grad(o.npix, pix, c, s, orc.Noise(taps=taps), m, d)
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32x2", 1e-10), ("f32", 1e-4)])
 def test_chi2_grad_matches_oracle(fx, dev, orc, c5, precision, tol):
     o, sky, taps, dtrue, d = c5
     delta = dtrue / 2
