@@ -139,18 +139,18 @@ __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict
                                                           float *__restrict__ c_out, float *__restrict__ s_out,
                                                           unsigned long long *__restrict__ n_invalid)
 {
-    __shared__ int qn;
+    __shared__ int qn, sdet_ok;
+    __shared__ float sdet[12];   // detector axes: d hi, d lo, o hi, o lo
     __shared__ int32_t queue[TILE];
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = obs[tl.obs];
     const int64_t gdet = ob.det_off + tl.det;
     const Quat qd = load_quat(q_det, gdet);
-    // detector axes (third and first columns of R(q_det)) in double-FP32
-    float dh[3], dl[3], oh[3], ol[3];
-    bool det_ok;
-    {
+    // detector axes (third and first columns of R(q_det)) in double-FP32, formed once per tile
+    // (FP64 work: one thread, not every thread of the CTA)
+    if (threadIdx.x == 0) {
         const double n2 = qd.w * qd.w + qd.x * qd.x + qd.y * qd.y + qd.z * qd.z;
-        det_ok = fabs(n2 - 1.0) <= 4.0 * 5.9604644775390625e-8;
+        sdet_ok = fabs(n2 - 1.0) <= 4.0 * 5.9604644775390625e-8;
         const double xx = qd.x * qd.x, yy = qd.y * qd.y, zz = qd.z * qd.z;
         const double xy = qd.x * qd.y, xz = qd.x * qd.z, yz = qd.y * qd.z;
         const double wx = qd.w * qd.x, wy = qd.w * qd.y, wz = qd.w * qd.z;
@@ -158,12 +158,17 @@ __global__ void __launch_bounds__(256) expand_fast_kernel(const Tile *__restrict
         const double ov[3] = {1.0 - 2.0 * (yy + zz), 2.0 * (xy + wz), 2.0 * (xz - wy)};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            dh[k] = (float)dv[k]; dl[k] = (float)(dv[k] - (double)dh[k]);
-            oh[k] = (float)ov[k]; ol[k] = (float)(ov[k] - (double)oh[k]);
+            const float h = (float)dv[k], g = (float)ov[k];
+            sdet[k] = h; sdet[3 + k] = (float)(dv[k] - (double)h);
+            sdet[6 + k] = g; sdet[9 + k] = (float)(ov[k] - (double)g);
         }
+        qn = 0;
     }
-    if (threadIdx.x == 0) qn = 0;
     __syncthreads();
+    float dh[3], dl[3], oh[3], ol[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { dh[k] = sdet[k]; dl[k] = sdet[3 + k]; oh[k] = sdet[6 + k]; ol[k] = sdet[9 + k]; }
+    const bool det_ok = sdet_ok != 0;
     const int64_t row = ob.tod_off + tl.det * ob.nsamp;
     for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
         const int64_t t = tl.t0 + k;
