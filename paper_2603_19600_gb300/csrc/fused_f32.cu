@@ -10,6 +10,7 @@
 // The time-ordered data never leaves the SM. The same skeleton gives the standalone N^-1,
 // the right-hand side P^T N^-1 d and chi^2 with its gradients.
 #include "tile.cuh"
+#include "pointing_fast.cuh"
 
 namespace fx {
 
@@ -19,10 +20,12 @@ namespace fx {
 // Samples of one tile (with halos) handled by each thread in the gather phases.
 constexpr int kPerThread = (TILE + 2 * kHalo + FT - 1) / FT;
 
+// bm (on the fly): boresight matrices of the certified FP32 pointing (pointing_fast.cuh).
 template <int MODE, int ACC, bool BANDED>
 __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
                                                           const float4 *__restrict__ x32, float4 *__restrict__ acc_hi,
-                                                          float4 *__restrict__ acc_lo, double *__restrict__ acc64)
+                                                          float4 *__restrict__ acc_lo, double *__restrict__ acc64,
+                                                          const float *__restrict__ bm)
 {
     extern __shared__ float fsm[];
     float *xs = fsm;                           // [XS] projected map P x over the tile and its halos
@@ -76,6 +79,65 @@ __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict
                 sc[spos(u)] = ck[k];
                 ss[spos(u)] = sk[k];
             }
+        }
+    } else if constexpr (MODE == FURAX_POINTING_ON_THE_FLY) {
+        // The pointing of the tile and its halos on the FP32 units, certified (pointing_fast.cuh);
+        // the samples the margins cannot certify take the exact FP64 recipe densely afterwards;
+        // then the map gathers. Pixels equal the recipe's; weights are FP32 (as in the FP32 cache).
+        __shared__ float sdet[12];
+        __shared__ int sdet_ok, qn;
+        if (threadIdx.x == 0) {
+            sdet_ok = det_axes_df(load_quat(pv.q_det, gdet), sdet);
+            qn = 0;
+        }
+        __syncthreads();
+        float dh[3], dl[3], oh[3], ol[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { dh[k] = sdet[k]; dl[k] = sdet[3 + k]; oh[k] = sdet[6 + k]; ol[k] = sdet[9 + k]; }
+        float2 psf = make_float2(1.f, 0.f);   // the detector's offset rotation, rounded once
+        if (pv.psi_cs) psf = make_float2((float)pv.psi_cs[gdet].x, (float)pv.psi_cs[gdet].y);
+        int32_t *queue = reinterpret_cast<int32_t *>(xs);   // xs is written only after the pointing
+        for (int u = threadIdx.x; u < nload; u += FT) {
+            const int64_t t = t_first + u;
+            float c = 0.f, s = 0.f;
+            int32_t pix = -1;
+            if (t >= 0 && t < ob.nsamp) {
+                if (sdet_ok &&
+                    certified_sample(bm + 18 * (ob.bore_off + t), dh, dl, oh, ol, (int32_t)ob.nside, pix, c, s)) {
+                    if (pv.hwp_cs) apply_hwp<float>(c, s, pv.hwp_cs[ob.bore_off + t]);
+                    if (pv.psi_cs) {
+                        const float c1 = c * psf.x - s * psf.y, s1 = s * psf.x + c * psf.y;
+                        c = c1;
+                        s = s1;
+                    }
+                } else {
+                    pix = -1;
+                    queue[atomicAdd(&qn, 1)] = u;
+                }
+            }
+            spix[spos(u)] = pix;
+            sc[spos(u)] = c;
+            ss[spos(u)] = s;
+        }
+        __syncthreads();
+        const int nq = qn;
+        for (int j = threadIdx.x; j < nq; j += FT) {
+            const int u = queue[j];
+            float c, s;
+            const int32_t pix = get_sample<0, float>(pv, ob, tl.det, t_first + u, c, s);
+            spix[spos(u)] = pix;
+            sc[spos(u)] = c;
+            ss[spos(u)] = s;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < nload; u += FT) {
+            const int32_t pix = spix[spos(u)];
+            float v = 0.f;
+            if (pix >= 0) {
+                const float4 m = __ldg(x32 + ob.map_off + pix);
+                v = fmaf(m.z, ss[spos(u)], fmaf(m.y, sc[spos(u)], m.x));
+            }
+            xs[spos(u)] = v;
         }
     } else {
         for (int u = threadIdx.x; u < nload; u += FT) {
@@ -136,14 +198,15 @@ static furax_status dispatch_fused_f32_acc(const furax_pointing *p, const furax_
     const unsigned g = (unsigned)p->n_tiles;
     const PointingView pv = p->view();
     const NoiseView nv = n->view();
+    const float *bm = MODE == FURAX_POINTING_ON_THE_FLY ? p->ws_bore_m : nullptr;
     if (acc == FURAX_ACC_F32)
         return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F32, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv, x32,
-                          hi, lo, a64);
+                          hi, lo, a64, bm);
     if (acc == FURAX_ACC_F32_KAHAN)
         return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F32_KAHAN, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv,
-                          x32, hi, lo, a64);
+                          x32, hi, lo, a64, bm);
     return launch_dyn(fused_f32_kernel<MODE, FURAX_ACC_F64, BANDED>, g, FT, kF32Smem, st, p->d_tiles, pv, nv, x32, hi,
-                      lo, a64);
+                      lo, a64, bm);
 }
 
 template <int MODE>
@@ -166,7 +229,17 @@ furax_status launch_fused_f32(const furax_pointing *p, const furax_noise *n, con
     furax_status rc;
     if (ft && !fused_f32_projects_templates(p))
         return set_error(FURAX_EINVAL, "template work is fused only for the cached FP32 pointing");
-    if (p->mode == FURAX_POINTING_ON_THE_FLY) rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
+    if (p->mode == FURAX_POINTING_ON_THE_FLY) {
+        // the boresight matrices of the certified pointing, from the handle's current quaternions
+        furax_pointing *pm = const_cast<furax_pointing *>(p);
+        if ((rc = ensure_ws(pm, (void **)&pm->ws_bore_m, sizeof(float) * 18 * std::max<int64_t>(1, p->nbore_total))))
+            return rc;
+        const unsigned bg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->nbore_total + 255) / 256, 16LL * p->n_sm));
+        bore_matrix_kernel<<<bg, 256, 0, st>>>(p->q_bore, p->nbore_total, pm->ws_bore_m);
+        count_launches(1);
+        if ((rc = check_launch("boresight matrices"))) return rc;
+        rc = dispatch_fused_f32<0>(p, n, x32, acc, hi, lo, a64, st);
+    }
     else if ((p->mode == FURAX_POINTING_CACHE_F32 || p->mode == FURAX_POINTING_CACHE_MIXED) && !ft &&
              sorted_active(p) && !long_band(n))
         rc = launch_fused_sorted(p, n, x32, acc, hi, lo, a64, st);   // pixel-sorted schedule
