@@ -105,11 +105,7 @@ __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict
                 if (sdet_ok &&
                     certified_sample(bm + 18 * (ob.bore_off + t), dh, dl, oh, ol, (int32_t)ob.nside, pix, c, s)) {
                     if (pv.hwp_cs) apply_hwp<float>(c, s, pv.hwp_cs[ob.bore_off + t]);
-                    if (pv.psi_cs) {
-                        const float c1 = c * psf.x - s * psf.y, s1 = s * psf.x + c * psf.y;
-                        c = c1;
-                        s = s1;
-                    }
+                    if (pv.psi_cs) rotate_psi_f(c, s, psf.x, psf.y);
                 } else {
                     pix = -1;
                     queue[atomicAdd(&qn, 1)] = u;
@@ -120,12 +116,19 @@ __global__ void __launch_bounds__(FT, 3) fused_f32_kernel(const Tile *__restrict
             ss[spos(u)] = s;
         }
         __syncthreads();
+        // the exact recipe as in the cache fill: FP64 weights (half-wave plate in FP64) rounded to
+        // FP32, then the offset rotation in FP32 like every other sample
         const int nq = qn;
+        const Quat qd = load_quat(pv.q_det, gdet);
         for (int j = threadIdx.x; j < nq; j += FT) {
             const int u = queue[j];
-            float c, s;
-            const int32_t pix = get_sample<0, float>(pv, ob, tl.det, t_first + u, c, s);
-            spix[spos(u)] = pix;
+            const int64_t t = t_first + u;
+            const SampleF64 r = point_f64(load_quat(pv.q_bore, ob.bore_off + t), qd, ob.nside);
+            double cd = r.c, sd = r.s;
+            if (pv.hwp_cs && r.pix >= 0) apply_hwp<double>(cd, sd, pv.hwp_cs[ob.bore_off + t]);
+            float c = (float)cd, s = (float)sd;
+            if (pv.psi_cs && r.pix >= 0) rotate_psi_f(c, s, psf.x, psf.y);
+            spix[spos(u)] = r.pix;
             sc[spos(u)] = c;
             ss[spos(u)] = s;
         }

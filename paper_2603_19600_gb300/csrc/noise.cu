@@ -176,11 +176,7 @@ __device__ __forceinline__ int32_t sample_f32(const PointingView &pv, const ObsI
         const int32_t pix = pv.pix[i];
         if constexpr (MODE == 2) { c = f64_to_f32_bits(pv.c64[i]); s = f64_to_f32_bits(pv.s64[i]); }
         else { c = pv.c32[i]; s = pv.s32[i]; }
-        if (pv.psi_cs && pix >= 0) {
-            const float c1 = c * csf.x - s * csf.y, s1 = s * csf.x + c * csf.y;
-            c = c1;
-            s = s1;
-        }
+        if (pv.psi_cs && pix >= 0) rotate_psi_f(c, s, csf.x, csf.y);
         return pix;
     }
 }

@@ -172,14 +172,27 @@ __device__ __forceinline__ Quat load_quat(const double *q, int64_t i)
     return Quat{lo.x, lo.y, hi.x, hi.y};
 }
 
+// FP32 rotation with explicit roundings, so that every kernel performs the same operations
+// whatever the compiler's contraction choices: c' = fma(c, c2, -(s s2)), s' = fma(s, c2, c s2).
+__device__ __forceinline__ void rotate_psi_f(float &c, float &s, float c2, float s2)
+{
+    const float c1 = __fmaf_rn(c, c2, -__fmul_rn(s, s2));
+    const float s1 = __fmaf_rn(s, c2, __fmul_rn(c, s2));
+    c = c1; s = s1;
+}
+
 // Rotate (c, s) = (cos 2psi, sin 2psi) by the detector offset: (cos 2(psi+delta), sin 2(psi+delta)).
 template <typename T>
 __device__ __forceinline__ void rotate_psi(T &c, T &s, double2 cs)
 {
-    T c2 = (T)cs.x, s2 = (T)cs.y;
-    T c1 = c * c2 - s * s2;
-    T s1 = s * c2 + c * s2;
-    c = c1; s = s1;
+    if constexpr (sizeof(T) == 4) {
+        rotate_psi_f(c, s, (float)cs.x, (float)cs.y);
+    } else {
+        T c2 = (T)cs.x, s2 = (T)cs.y;
+        T c1 = c * c2 - s * s2;
+        T s1 = s * c2 + c * s2;
+        c = c1; s = s1;
+    }
 }
 
 // Ideal half-wave plate at angle w in front of the detector (HWPOperator, Table 3 of the Furax
@@ -192,9 +205,15 @@ template <typename T>
 __device__ __forceinline__ void apply_hwp(T &c, T &s, double2 h)
 {
     const T c4 = (T)h.x, s4 = (T)h.y;
-    const T c1 = c4 * c + s4 * s;
-    const T s1 = s4 * c - c4 * s;
-    c = c1; s = s1;
+    if constexpr (sizeof(T) == 4) {   // explicit roundings, as in rotate_psi_f
+        const float c1 = __fmaf_rn(c4, c, __fmul_rn(s4, s));
+        const float s1 = __fmaf_rn(s4, c, -__fmul_rn(c4, s));
+        c = c1; s = s1;
+    } else {
+        const T c1 = c4 * c + s4 * s;
+        const T s1 = s4 * c - c4 * s;
+        c = c1; s = s1;
+    }
 }
 
 // Per-sample pointing from a PointingView, for each storage mode.

@@ -237,3 +237,24 @@ def test_blockdiag_singular_blocks_match_oracle(fx, dev, orc, repeats, mode):
     v = bj["valid"].cpu().numpy()
     idx = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
     assert np.all(np.linalg.eigvalsh(bj["inv"].cpu().numpy()[v][:, idx])[:, 0] > 0)
+
+
+@pytest.mark.parametrize("hwp", [False, True])
+def test_on_the_fly_fp32_operator_equals_cached(fx, dev, prob, hwp):
+    """The on-the-fly FP32 operator evaluates the pointing with the certified FP32 method of the
+    FP32 cache fill (the exact FP64 recipe where the margins cannot certify): pixels and weights,
+    hence the operator, equal the cached FP32 operator's up to the order of the FP64 additions;
+    with per-detector angle offsets and an ideal half-wave plate too."""
+    o, *_ , taps, _ = prob
+    w = torch.as_tensor(synth.hwp_angle(o.nsamp), device=dev) if hwp else None
+    delta = torch.as_tensor(np.radians(np.linspace(-1.0, 1.0, o.ndet)), device=dev)
+    qb = torch.as_tensor(o.q_bore, device=dev)
+    qd = torch.as_tensor(o.q_det, device=dev)
+    x = torch.as_tensor(synth.gaussian_sky(o.nside, synth.rng(7, 8)), device=dev)
+    out = {}
+    for mode in ("on_the_fly", "cache_f32"):
+        P = fx.Pointing(qb, qd, [o.ndet], [o.nsamp], [o.nside], mode=mode, psi_offset=delta, hwp_angle=w)
+        N = fx.Noise.banded(P, taps)
+        out[mode] = fx.ptnp_apply(P, N, x, None, "f32", "f64").cpu().numpy()
+        P.close()
+    assert rel(out["on_the_fly"], out["cache_f32"]) < 1e-12
