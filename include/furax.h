@@ -484,7 +484,8 @@ furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink, double *fl
  * error into table[ntable + idx], so table holds 2 ntable float4), 3 three FP64 reductions
  * (table holds [ntable][3] doubles), 4 the same into 32-byte records ([ntable][4] doubles), 5 the
  * kind-3 reductions issued by three consecutive lanes of one instruction per index ([ntable][3]),
- * 6 kind 5 and 7 kind 0 with 8 operations per thread in flight (index loads first).
+ * 6 kind 5 and 7 kind 0 with 8 operations per thread in flight (index loads first), 8 kind 5 with
+ * 64-bit integer reductions (table: 3 ntable 64-bit words).
  * Grid of 8 x 256 threads per SM; the caller times it. The indices are not checked on the device.
  * sink: one float of device scratch. */
 furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable, void *sink,

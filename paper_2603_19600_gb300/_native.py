@@ -321,7 +321,7 @@ def furax_probe_l2(kind: int, idx, table, ntable: int, sink, stream=None) -> Non
     if idx.numel() and (int(idx.min()) < 0 or int(idx.max()) >= ntable):
         raise ValueError("probe indices must lie in [0, ntable)")
     need = {0: 16 * ntable, 1: 16 * ntable, 2: 32 * ntable, 3: 24 * ntable, 4: 32 * ntable, 5: 24 * ntable,
-            6: 24 * ntable, 7: 16 * ntable}[int(kind)]
+            6: 24 * ntable, 7: 16 * ntable, 8: 24 * ntable}[int(kind)]
     if table.numel() * table.element_size() < need:
         raise ValueError(f"probe table needs {need} bytes")
     _call("furax_probe_l2", int(kind), _ptr(idx, torch.int32, None, "idx"), idx.numel(), _ptr(table, None, None, "table"),

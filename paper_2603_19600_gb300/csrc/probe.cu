@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(PB) probe_fma_x2_kernel(int64_t iters, float b
 // adds component c of index k), so that one warp instruction covers a pixel's whole record;
 // 6 kind 5 and 7 kind 0 with kProbeBatch operations per thread in flight (all index loads, then
 // all gathers or reductions), so that the L2, not the latency of a thread's index load, sets the
-// rate.
+// rate; 8 kind 5 with 64-bit integer reductions (red.add.u64) instead of FP64 ones.
 constexpr int kProbeBatch = 8;
 __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *__restrict__ idx, int64_t n,
                                                       float4 *__restrict__ t4, double *__restrict__ t64, int64_t ntab,
@@ -106,6 +106,16 @@ __global__ void __launch_bounds__(PB) probe_l2_kernel(int kind, const int32_t *_
             }
         }
         if (acc == 12345.f) sink[0] = acc;
+        return;
+    }
+    if (kind == 8) {
+        unsigned long long *t = reinterpret_cast<unsigned long long *>(t64);
+        for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < 3 * n; f += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = f / 3;
+            const int c = (int)(f - 3 * i);
+            asm volatile("red.global.add.u64 [%0], %1;" ::"l"(t + 3 * (int64_t)idx[i] + c), "l"((unsigned long long)(c + 1))
+                         : "memory");
+        }
         return;
     }
     if (kind == 5) {
@@ -173,7 +183,7 @@ extern "C" furax_status furax_probe_fma(int32_t kind, int64_t iters, void *sink,
 extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t n, void *table, int64_t ntable,
                                        void *sink, void *stream)
 {
-    if (kind < 0 || kind > 7) return set_error(FURAX_EINVAL, "kind must be in [0, 7]");
+    if (kind < 0 || kind > 8) return set_error(FURAX_EINVAL, "kind must be in [0, 8]");
     if (!idx || !table || !sink || n < 0 || ntable < 1) return set_error(FURAX_EINVAL, "invalid probe arguments");
     if (n == 0) return FURAX_OK;
     int dev = 0, sms = 1;
@@ -181,7 +191,8 @@ extern "C" furax_status furax_probe_l2(int32_t kind, const int32_t *idx, int64_t
     if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     if (rc) return rc;
     // indices are the caller's: each must lie in [0, ntable) (float4 kinds: table holds 2 ntable
-    // float4 for kind 2; kinds 3, 5, 6: 3 ntable doubles; kind 4: 4 ntable doubles)
+    // float4 for kind 2; kinds 3, 5, 6: 3 ntable doubles, kind 8 3 ntable 64-bit integers; kind 4: 4
+    // ntable doubles)
     const unsigned g = (unsigned)std::min<int64_t>((n + PB - 1) / PB, 8LL * sms);
     probe_l2_kernel<<<g, PB, 0, (cudaStream_t)stream>>>(kind, idx, n, (float4 *)table, (double *)table, ntable,
                                                          (float *)sink);
