@@ -69,3 +69,28 @@ def test_autograd_function_and_finite_differences(fx, dev, orc, c5):
             fm = fx.chi2(m, delta - e, P, N, dd).item()
         fd = (fp - fm) / (2 * h)
         assert abs(fd - gd[j].item()) <= 1e-5 * max(abs(gd[j].item()), 1e-3 * chi2 * h)
+
+
+@pytest.mark.parametrize("mode", ["on_the_fly", "cache_mixed"])
+@pytest.mark.parametrize("noise", ["banded", "white"])
+def test_chi2_grad_double_fp32_and_fp32_across_modes(fx, dev, orc, c5, mode, noise):
+    """The double-FP32 χ² and gradients (FP64-accurate weights: on the fly or the mixed cache)
+    match the oracle to FP64-like accuracy, and the FP32 ones to FP32 accuracy, for a band and for
+    white noise."""
+    o, sky, taps, dtrue, d = c5
+    delta = dtrue / 2
+    m = sky * 1.01
+    sigma2 = np.linspace(0.5, 1.5, o.ndet)
+    on = orc.Noise(taps=taps) if noise == "banded" else orc.Noise(sigma2=sigma2)
+    pix, c, s, _ = orc.pointing(o.nside, o.q_bore, o.q_det, delta)
+    chi2, gm, gp = orc.chi2_grad(o.npix, pix, c, s, on, m, d)
+    o.psi_offset = delta
+    P = fx.Pointing.from_observations([o], mode=mode, device=dev)
+    N = fx.Noise.banded(P, taps) if noise == "banded" else fx.Noise.white(P, sigma2)
+    dd = torch.as_tensor(d.ravel(), device=dev)
+    for precision, tol, data in (("f32x2", 1e-10, dd), ("f32", 1e-4, dd.float())):
+        c2, gmap, gpsi = fx.chi2_grad(P, N, data, torch.as_tensor(m, device=dev), precision)
+        assert abs(c2.item() - chi2) <= tol * chi2, precision
+        assert np.linalg.norm(gmap.cpu().numpy() - gm) <= tol * np.linalg.norm(gm) * 10, precision
+        assert np.max(np.abs(gpsi.cpu().numpy() - gp)) <= tol * np.max(np.abs(gp)) * 10, precision
+    o.psi_offset = None
