@@ -61,7 +61,9 @@ __device__ __forceinline__ void band_product_df(const float *__restrict__ xh, co
 
 constexpr size_t kDfSmem = sizeof(float) * (2 * XS + 2 * MAXTAPS) + sizeof(float2) * 2 * CS + sizeof(int32_t) * CS;
 
-// acc64 += P^T N^-1 P x  (x: FP64 [npix][3], zero on masked pixels), or acc64 += P^T N^-1 d (FROM_TOD).
+// acc64 += P^T N^-1 d (FROM_TOD: the right-hand side from FP64 data, the form launched), or
+// acc64 += P^T N^-1 P x (x: FP64 [npix][3]); the map form is served by df_apply_kernel below, which
+// issues no FP64 arithmetic per sample.
 template <int MODE, bool BANDED, bool FROM_TOD, typename DT>
 __global__ void __launch_bounds__(FT, 2) fused_df_kernel(const Tile *__restrict__ tiles, PointingView pv, NoiseView nv,
                                                          const double *__restrict__ x, const DT *__restrict__ d,
