@@ -86,4 +86,14 @@ __device__ __forceinline__ float f64_to_f32_bits(double v)
     return __uint_as_float((uint32_t)(b >> 63) << 31 | r);
 }
 
+// Conversion between FP32 and FP64 with the hardware's result (exact widening, round-to-nearest-
+// even narrowing) but, for FP32 <-> FP64, from the encodings on the integer pipe.
+template <typename To, typename From>
+__device__ __forceinline__ To convert_bits(From v)
+{
+    if constexpr (sizeof(To) == 8 && sizeof(From) == 4) return f32_to_f64_bits(v);
+    else if constexpr (sizeof(To) == 4 && sizeof(From) == 8) return f64_to_f32_bits(v);
+    else return (To)v;
+}
+
 }  // namespace fx

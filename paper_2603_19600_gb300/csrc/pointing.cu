@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) P_kernel(const Tile *__restrict__ tiles, 
             const MT *m = map + 3 * (ob.map_off + pix);
             v = (T)m[0] + (T)m[1] * c + (T)m[2] * s;
         }
-        tod[ob.tod_off + tl.det * ob.nsamp + t] = (TT)v;
+        tod[ob.tod_off + tl.det * ob.nsamp + t] = convert_bits<TT>(v);
     }
 }
 
@@ -168,18 +168,41 @@ __global__ void __launch_bounds__(256) PT_kernel(const Tile *__restrict__ tiles,
 {
     const Tile tl = tiles[blockIdx.x];
     const ObsInfo ob = pv.obs[tl.obs];
+    if constexpr (ACC == FURAX_ACC_F64) {
+        // three FP64 sums per sample, issued as whole pixel records by the warp (launched with
+        // 256 threads: eight staging areas); warp-uniform trip count
+        __shared__ double stage[8][96];
+        __shared__ int32_t spx[8][32];
+        const int warp = threadIdx.x >> 5;
+        double *base = acc64 + 3 * ob.map_off;
+        for (int kw = threadIdx.x & ~31; kw < tl.len; kw += blockDim.x) {
+            const int k = kw + (threadIdx.x & 31);
+            int32_t pix = -1;
+            double v[3] = {0.0, 0.0, 0.0};
+            if (k < tl.len) {
+                const int64_t t = tl.t0 + k;
+                T c, s;
+                pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
+                if (pix >= 0) {
+                    const T y = convert_bits<T>(tod[ob.tod_off + tl.det * ob.nsamp + t]);
+                    v[0] = (double)y;
+                    v[1] = (double)(y * c);
+                    v[2] = (double)(y * s);
+                }
+            }
+            red_add_f64_records_warp<3, double>(base, pix, v, stage[warp], spx[warp]);
+            if (hits && pix >= 0) red_add_s32(hits + ob.map_off + pix, 1);
+        }
+        return;
+    }
     for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
         const int64_t t = tl.t0 + k;
         T c, s;
         const int32_t pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
         if (pix < 0) continue;
         const int64_t gp = ob.map_off + pix;
-        const T y = (T)tod[ob.tod_off + tl.det * ob.nsamp + t];
-        if constexpr (ACC == FURAX_ACC_F64) {
-            red_add_f64(acc64 + 3 * gp + 0, (double)y);
-            red_add_f64(acc64 + 3 * gp + 1, (double)(y * c));
-            red_add_f64(acc64 + 3 * gp + 2, (double)(y * s));
-        } else if constexpr (ACC == FURAX_ACC_F32) {
+        const T y = convert_bits<T>(tod[ob.tod_off + tl.det * ob.nsamp + t]);
+        if constexpr (ACC == FURAX_ACC_F32) {
             red_add_v4(hi + gp, make_float4((float)y, (float)(y * c), (float)(y * s), 0.f));
         } else {
             kahan_add_v4(hi + kKahanStride * gp, lo + kKahanStride * gp,
