@@ -387,6 +387,31 @@ __global__ void __launch_bounds__(FT) tpl_scatter_kernel(const Tile *__restrict_
 #pragma unroll
     for (int l = 0; l < 4; ++l) bv[l] = T(tv.b[4 * gdet + l]);
     const TplPoly<T> pl(tv, gdet, ob.nsamp, bv);
+    if constexpr (ACC == FURAX_ACC_F64) {
+        // three FP64 sums per sample, issued as whole pixel records by the warp (values of type
+        // T, widened after the exchange); warp-uniform trip count
+        __shared__ T stage[FT / 32][96];
+        __shared__ int32_t spx[FT / 32][32];
+        double *base = acc64 + 3 * ob.map_off;
+        for (int uw = threadIdx.x & ~31; uw < tl.len; uw += FT) {
+            const int u = uw + (threadIdx.x & 31);
+            int32_t pix = -1;
+            T v3[3] = {T(0), T(0), T(0)};
+            if (u < tl.len) {
+                const int64_t t = tl.t0 + u;
+                T c, s;
+                pix = get_sample<MODE, T>(pv, ob, tl.det, t, c, s);
+                if (pix >= 0) {
+                    const T v = -tpl_value<T>(nv, tv, gdet, ob.nsamp, t, bv, pl);
+                    v3[0] = v;
+                    v3[1] = v * c;
+                    v3[2] = v * s;
+                }
+            }
+            red_add_f64_records_warp<3, T>(base, pix, v3, stage[threadIdx.x >> 5], spx[threadIdx.x >> 5]);
+        }
+        return;
+    }
     for (int u = threadIdx.x; u < tl.len; u += FT) {
         const int64_t t = tl.t0 + u;
         T c, s;
@@ -396,13 +421,9 @@ __global__ void __launch_bounds__(FT) tpl_scatter_kernel(const Tile *__restrict_
         const int64_t gp = ob.map_off + pix;
         if constexpr (ACC == FURAX_ACC_F32) {
             red_add_v4(hi + gp, make_float4(float(v), float(v * c), float(v * s), 0.f));
-        } else if constexpr (ACC == FURAX_ACC_F32_KAHAN) {
+        } else {
             kahan_add_v4(hi + kKahanStride * gp, lo + kKahanStride * gp,
                          make_float4(float(v), float(v * c), float(v * s), 0.f));
-        } else {
-            red_add_f64(acc64 + 3 * gp + 0, (double)v);
-            red_add_f64(acc64 + 3 * gp + 1, (double)(v * c));
-            red_add_f64(acc64 + 3 * gp + 2, (double)(v * s));
         }
     }
 }
